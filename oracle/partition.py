@@ -1,0 +1,165 @@
+"""Disjoint and overlapping subdomains and their node sets (Secs. 3, 4.1, 4.2, 5.2.2).
+
+Disjoint split (replaces METIS, Sec. 3.1): recursive coordinate bisection of the closest
+points of Sigma_A.  At a bisection-tree node holding n points and leaves [l0, l1):
+  axis = the coordinate of largest extent of the points' CP bounding box (ties: x < y < z);
+  points ordered by (CP[axis], global index);
+  left leaves [l0, l0 + P//2), n_left = floor(n * W_left / W) with integer leaf weights.
+Overlap (Sec. 4.1): Sigma_j = active nodes within N_O steps of the disjoint set in the
+  6-neighbour graph on Sigma_A; the last layer is BFS distance exactly N_O.
+Sigma_j^G (Sec. 4.1): ghost nodes among the 6-neighbours of Sigma_j.
+Sigma_j^BC (Sec. 4.1): active nodes completing the 7-point stencils of Sigma_j and the
+  interpolation stencils of CP(x), x in Sigma_j u Sigma_j^G, that are not in Sigma_j;
+  for Robin conditions also the ghost layer N6(Sigma_j^{BC,A}) \\ (everything above).
+Lambda_j (Sec. 4.2): CP(x) for x in the last overlap layer, tagged by x's global index.
+CP_{S_j}(x_i) (Eq. locCP): the point of Lambda_j nearest to x_i (ties: lowest tag).
+Cross-point nodes (Sec. 5.2.2 of the method, "Modified scheme for cross points"): active
+  nodes whose active 6-neighbours carry >= 2 labels other than their own; BC nodes within
+  2 N_O h of any of them (squared integer grid distance <= (2 N_O)^2) use alpha_x.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from .band import NBR_OFFSETS
+
+
+def rcb(points: np.ndarray, n_sub: int, leaf_weights=None) -> np.ndarray:
+    """Labels in [0, n_sub) for each point (recursive coordinate bisection)."""
+    n = len(points)
+    w = np.ones(n_sub, dtype=np.int64) if leaf_weights is None else np.asarray(leaf_weights, np.int64)
+    labels = np.full(n, -1, dtype=np.int64)
+    stack = [(np.arange(n, dtype=np.int64), 0, n_sub)]
+    while stack:
+        idx, l0, l1 = stack.pop()
+        P = l1 - l0
+        if P == 1:
+            labels[idx] = l0
+            continue
+        pts = points[idx]
+        ext = pts.max(axis=0) - pts.min(axis=0)
+        axis = int(np.argmax(ext))                 # first maximum: x < y < z
+        order = np.lexsort((idx, pts[:, axis]))    # primary CP[axis], secondary index
+        sidx = idx[order]
+        PL = P // 2
+        WL = int(w[l0:l0 + PL].sum())
+        W = int(w[l0:l1].sum())
+        nL = (len(idx) * WL) // W
+        stack.append((sidx[nL:], l0 + PL, l1))
+        stack.append((sidx[:nL], l0, l0 + PL))
+    return labels
+
+
+@dataclasses.dataclass
+class Subdomain:
+    j: int
+    own: np.ndarray         # disjoint set  (global active indices, sorted)
+    sigma: np.ndarray       # overlapping set Sigma_j (sorted)
+    last: np.ndarray        # last overlap layer (sorted)
+    ghost: np.ndarray       # Sigma_j^G (global node indices >= N_A, sorted)
+    bc_a: np.ndarray        # Sigma_j^{BC} active part (sorted)
+    bc_g: np.ndarray        # Robin ghost layer around bc_a (global node indices, sorted)
+
+
+def bfs_layers(band, labels: np.ndarray, j: int, n_overlap: int) -> np.ndarray:
+    """BFS distance (or -1) from the disjoint set j over the active 6-neighbour graph."""
+    n_a = band.n_active
+    dist = np.full(n_a, -1, dtype=np.int64)
+    front = np.flatnonzero(labels == j)
+    dist[front] = 0
+    for layer in range(1, n_overlap + 1):
+        cand = band.nbr[front].ravel()
+        cand = np.unique(cand[cand < n_a])
+        cand = cand[dist[cand] < 0]
+        dist[cand] = layer
+        front = cand
+    return dist
+
+
+def stencil_nodes(E, rows: np.ndarray) -> np.ndarray:
+    """Union of the interpolation stencils (active columns of E) of the given rows."""
+    if len(rows) == 0:
+        return np.zeros(0, dtype=np.int64)
+    return np.unique(E.tocsr()[rows].indices).astype(np.int64)
+
+
+def build_subdomain(band, E, labels, j: int, n_overlap: int, robin: bool) -> Subdomain:
+    n_a = band.n_active
+    dist = bfs_layers(band, labels, j, n_overlap)
+    sigma = np.flatnonzero(dist >= 0)
+    last = np.flatnonzero(dist == n_overlap)
+    in_sigma = dist >= 0
+    nb = band.nbr[sigma].ravel()
+    ghost = np.unique(nb[nb >= n_a])
+    act_nb = np.unique(nb[nb < n_a])
+    act_nb = act_nb[~in_sigma[act_nb]]
+    sten = stencil_nodes(E, np.concatenate([sigma, ghost]))
+    sten = sten[~in_sigma[sten]]
+    bc_a = np.union1d(act_nb, sten)
+    if robin:
+        nb2 = np.unique(band.nbr[bc_a].ravel())
+        taken = np.concatenate([sigma, ghost, bc_a])
+        bc_g = np.setdiff1d(nb2, taken)
+    else:
+        bc_g = np.zeros(0, dtype=np.int64)
+    return Subdomain(j, np.flatnonzero(labels == j), sigma, last, ghost, bc_a, bc_g)
+
+
+def cross_point_nodes(band, labels: np.ndarray) -> np.ndarray:
+    """Active nodes with active 6-neighbours in >= 2 subdomains other than their own."""
+    n_a = band.n_active
+    nl = np.where(band.nbr < n_a, labels[np.minimum(band.nbr, n_a - 1)], -1)
+    nl = np.where(nl == labels[:, None], -1, nl)
+    s = np.sort(nl, axis=1)
+    distinct = (s >= 0) & np.concatenate([np.ones((n_a, 1), bool), s[:, 1:] != s[:, :-1]], axis=1)
+    return np.flatnonzero(distinct.sum(axis=1) >= 2)
+
+
+class CrossMarks:
+    """Grid nodes within 2 N_O grid steps (Euclidean, inclusive) of any cross-point node."""
+
+    def __init__(self, band, cross: np.ndarray, n_overlap: int):
+        self.band = band
+        rad = 2 * n_overlap
+        self.lo = band.ijk.min(0) - rad
+        hi = band.ijk.max(0) + rad
+        self.mark = np.zeros(tuple((hi - self.lo + 1).tolist()), dtype=bool)
+        if len(cross) == 0:
+            return
+        r = np.arange(-rad, rad + 1)
+        A, B, C = np.meshgrid(r, r, r, indexing="ij")
+        ball = np.stack([A.ravel(), B.ravel(), C.ravel()], 1)
+        ball = ball[(ball * ball).sum(1) <= rad * rad]
+        cij = band.ijk[cross] - self.lo
+        for off in ball:                     # dilate the cross points by the integer ball
+            q = cij + off
+            self.mark[q[:, 0], q[:, 1], q[:, 2]] = True
+
+    def __call__(self, nodes: np.ndarray) -> np.ndarray:
+        qn = self.band.ijk[nodes] - self.lo
+        return self.mark[qn[:, 0], qn[:, 1], qn[:, 2]]
+
+
+def effective_boundary_cp(band, sub: Subdomain, nodes: np.ndarray):
+    """CP_{S_j}(x) for the given nodes (Eq. locCP, BC line): nearest point of Lambda_j.
+
+    Returns (points (M,3), generator global index (M,))."""
+    lam_pts = band.cp[sub.last]
+    X = band.coords(nodes)
+    best = np.empty(len(nodes), dtype=np.int64)
+    for s in range(0, len(nodes), 2048):       # exhaustive argmin in chunks
+        Xc = X[s:s + 2048]
+        D = Xc[:, None, :] - lam_pts[None, :, :]
+        d2 = (D[..., 0] * D[..., 0] + D[..., 1] * D[..., 1]) + D[..., 2] * D[..., 2]
+        best[s:s + 2048] = np.argmin(d2, axis=1)   # first minimum = lowest tag
+    return lam_pts[best], sub.last[best]
+
+
+def all_subdomains(band, E, labels, n_sub: int, n_overlap: int, robin: bool):
+    return [build_subdomain(band, E, labels, j, n_overlap, robin) for j in range(n_sub)]
+
+
+__all__ = ["rcb", "Subdomain", "bfs_layers", "build_subdomain", "cross_point_nodes",
+           "CrossMarks", "effective_boundary_cp", "all_subdomains", "NBR_OFFSETS"]
