@@ -1,0 +1,208 @@
+/*
+ * cpm.h — C ABI of the GB300 RAS/ORAS closest-point-method solver.
+ *
+ * Method: May, Haynes & Ruuth, "Schwarz solvers and preconditioners for the closest point
+ * method" (arXiv:1909.08734).  The library solves (c - Lap_S) u = f on a surface S through
+ * the stabilised CPM discretisation (Sec. 2.1, Eq. impLapBel) with right-preconditioned
+ * flexible GMRES, the preconditioner being restricted additive Schwarz with Dirichlet
+ * (RAS, Eq. simpleRAS / Eq. algRAS) or Robin (ORAS, Sec. 5.2, Eq. robfo) transmission
+ * conditions, including the cross-point modification (Sec. 5.2.2).
+ *
+ * Conventions for every call:
+ *  - Every call returns cpm_status; no exception, abort or exit crosses the ABI.
+ *    cpm_last_error() returns a thread-local message for the last failing call.
+ *  - Handles (cpm_band, cpm_partition, oras_precond) are opaque and library-owned; free
+ *    them with the matching *_destroy.  A handle is not thread-safe; distinct handles are.
+ *  - Vector arguments named *_dev are caller-owned DEVICE memory (FP64, contiguous, in
+ *    canonical band order: active node g = 0..N_A-1, right-hand sides as the slow
+ *    dimension).  The library never frees them.  Host arrays returned by *_info / getters
+ *    stay valid until the owning handle is destroyed.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Setup calls (cpm_build_band, cpm_partition) are host-only and never touch a GPU.
+ *    oras_setup synchronises its stream before returning.  cpm_op_apply and oras_apply
+ *    are asynchronous on the stream.  cpm_gmres_solve synchronises once per restart cycle.
+ */
+#ifndef CPM_H
+#define CPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CPM_OK = 0,
+  CPM_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, unsupported option            */
+  CPM_ERR_OOM = 2,           /* host or device allocation failed                      */
+  CPM_ERR_CUDA = 3,          /* a CUDA runtime call failed (message in cpm_last_error) */
+  CPM_ERR_SINGULAR = 4,      /* zero pivot in a local LU (subdomain in the message)   */
+  CPM_ERR_NOT_CONVERGED = 5, /* GMRES hit max_it before the tolerance                 */
+  CPM_ERR_BREAKDOWN = 6,     /* GMRES basis vector of norm 0 with a large residual    */
+  CPM_ERR_NAN = 7,           /* NaN or Inf in a norm                                  */
+  CPM_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up                    */
+  CPM_ERR_BUDGET = 9,        /* request exceeds a memory budget                       */
+  CPM_ERR_STENCIL = 10       /* an interpolation / FD stencil leaves its node set     */
+} cpm_status;
+
+/* surface kinds */
+enum { CPM_SPHERE = 0, CPM_TORUS = 1 };
+/* transmission conditions (oras_setup) */
+enum {
+  CPM_RAS = 0,      /* Dirichlet: A_j = R_j A R_j^T on Sigma_j (Eq. simpleRAS)              */
+  CPM_ORAS = 1,     /* Robin, every local unknown gets a 7-point row (reading R1)           */
+  CPM_ORAS_R3 = 2   /* Robin, boundary unknowns get (c+6/h^2) w - (6/h^2) T w (reading R3)  */
+};
+/* precision of the local factors and local solves */
+enum { CPM_FP64 = 0, CPM_FP32 = 1, CPM_BF16 = 2 };
+/* node-set selectors for cpm_partition_set */
+enum { CPM_SET_OWN = 0, CPM_SET_SIGMA = 1, CPM_SET_LAST = 2, CPM_SET_GHOST = 3,
+       CPM_SET_BC_A = 4, CPM_SET_BC_G = 5, CPM_SET_BC_GEN = 6, CPM_SET_BC_NEARX = 7 };
+
+/* Surface with an analytic closest point (Sec. 2.1): sphere of radius R at the origin, or
+ * the torus about the z axis with major radius R and minor radius r. */
+typedef struct {
+  int kind;
+  double R;
+  double r;
+} cpm_surface;
+
+typedef struct cpm_band cpm_band;
+typedef struct cpm_part cpm_part;
+typedef struct oras_precond oras_precond;
+
+typedef struct {
+  int64_t n_active;       /* N_A */
+  int64_t n_ghost;        /* N_G */
+  int p;                  /* interpolation degree */
+  double h;               /* grid spacing */
+  double lambda;          /* tube radius actually used */
+  const int32_t* ijk;     /* host, (N_A+N_G) x 3 integer grid coordinates, node x = ijk*h */
+  const double* cp;       /* host, (N_A+N_G) x 3 closest points CP_S(x) */
+  const int32_t* nbr;     /* host, N_A x 6 node indices of (-x,+x,-y,+y,-z,+z) neighbours */
+  const int32_t* base;    /* host, (N_A+N_G) x 3 lowest interpolation-stencil node of CP(x) */
+} cpm_band_info;
+
+/* Band construction (Sec. 2.1, tube-radius construction).
+ * Active nodes: grid nodes x = (i,j,k)h with ||x - CP_S(x)|| <= lambda, lambda =
+ * lambda_over_h * h; lambda_over_h <= 0 selects ((1.0033*sqrt(3))*(p+1))/2.  Ghost nodes:
+ * 6-neighbours of actives that are not active.  Canonical order: actives lexicographic in
+ * (i,j,k), k fastest, then ghosts in the same order.  Also computes each node's
+ * interpolation stencil base and 1-D barycentric weights at CP_S(x) (degree p in {2,3}).
+ * Errors: INVALID_ARG (h <= 0, p not 2 or 3, unknown surface), STENCIL (an interpolation
+ * stencil of some node leaves the active set: lambda too small), OOM.  Host only. */
+cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
+                          cpm_band** out);
+cpm_status cpm_band_info_get(const cpm_band* band, cpm_band_info* out);
+void cpm_band_destroy(cpm_band* band);
+
+/* Partition and overlapping node sets (Sec. 3.1 split, Sec. 4.1 overlap and boundary sets,
+ * Sec. 4.2 effective boundary, Sec. 5.2.2 cross points).
+ * Disjoint labels by recursive coordinate bisection of the actives' closest points with
+ * integer leaf weights (leaf_weights: n_sub host int64, NULL = equal).  Sigma_j = actives
+ * within n_overlap steps in the active 6-neighbour graph.  Builds Sigma_j^G, Sigma_j^BC
+ * (active part and the Robin ghost layer), Lambda_j, the nearest Lambda_j point of every
+ * boundary node (ties: lowest generator index) and the cross-point marks (boundary nodes
+ * within 2*n_overlap*h of a node with neighbours in >= 2 other subdomains).
+ * align_passes must be 0 (interface alignment of Sec. 3.2 is not built).
+ * Errors: INVALID_ARG (n_sub < 1, n_overlap < 0, a leaf weight <= 0, a subdomain left
+ * empty, align_passes != 0), OOM.  Host only. */
+cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
+                         int n_overlap, int align_passes, cpm_part** out);
+/* Labels of the N_A actives (host, int32, valid until destroy). */
+cpm_status cpm_partition_labels(const cpm_part* part, const int32_t** labels);
+/* One node set of subdomain j (CPM_SET_*), as a sorted host int32 array of global node
+ * indices (BC_GEN: generator of CP_{S_j} for each BC node, BC_A then BC_G order; BC_NEARX:
+ * 1 if that BC node uses alpha_x). */
+cpm_status cpm_partition_set(const cpm_part* part, int j, int which, const int32_t** data,
+                             int64_t* len);
+cpm_status cpm_partition_cross_points(const cpm_part* part, const int32_t** data,
+                                      int64_t* len);
+void cpm_partition_destroy(cpm_part* part);
+
+/* Local operator of subdomain j in coordinate form (host only, no GPU).  Local unknowns are
+ * Sigma_j (global order) and, for ORAS, Sigma_j^{BC,A} (global order).  RAS: A_j = R_j A
+ * R_j^T (Eq. simpleRAS).  ORAS: Eq. localOP with Robin extension rows at the boundary nodes
+ * (Eq. robfo; alpha_x near cross points).  Call with rows == NULL to get *nnz and *n; then
+ * with arrays of *nnz entries (row, col, value), duplicates already summed. */
+cpm_status cpm_local_coo(const cpm_band* band, const cpm_part* part, double c,
+                         int transmission, double alpha, double alpha_x, int j, int64_t* n,
+                         int64_t* nnz, int32_t* rows, int32_t* cols, double* vals);
+
+/* Preconditioner setup (Sec. 5 local operators; "local operators" phase of Sec. 6.6):
+ * uploads the band to the device, assembles every local matrix as a dense tile-major
+ * matrix on the GPU, factors all of them with partial pivoting in batched launches
+ * (precision CPM_FP64 / CPM_FP32 / CPM_BF16: BF16 inputs with FP32 accumulation, factors
+ * stored in BF16) and keeps the factors resident.  Synchronises the stream.
+ * Errors: INVALID_ARG, STENCIL, SINGULAR (zero pivot), OOM, CUDA. */
+cpm_status oras_setup(const cpm_band* band, const cpm_part* part, double c,
+                      int transmission, double alpha, double alpha_x, int precision,
+                      void* stream, oras_precond** out);
+
+typedef struct {
+  int n_sub;
+  int64_t n_active;
+  int64_t n_nodes;            /* N_A + N_G */
+  int precision;
+  int transmission;
+  int64_t max_n;              /* largest local size n_j */
+  int64_t sum_n;              /* sum of n_j */
+  int64_t sum_n2;             /* sum of n_j^2 (algorithmic factor entries) */
+  int64_t sum_sigma;          /* sum of |Sigma_j| (restrict reads) */
+  int64_t factor_bytes;       /* device bytes of the resident factors */
+  int64_t device_bytes;       /* all device bytes held by the handle */
+  double setup_ms_assemble;   /* device time of the assembly launch(es) */
+  double setup_ms_factor;     /* device time of the batched LU launches */
+} oras_info;
+cpm_status oras_info_get(const oras_precond* pc, oras_info* out);
+/* Local sizes n_j (host array of n_sub int64 written by the call). */
+cpm_status oras_local_sizes(const oras_precond* pc, int64_t* n_out);
+
+/* y = A x (Eq. impLapBel with A = cI - Lap_S^h), FP64, matrix-free over the band:
+ * v_k = sum (wx_a wy_b wz_c) x[stencil(k)] for every band node k, then
+ * y_i = (c + 6/h^2) x_i - (1/h^2) sum_{6 neighbours} v_k.  x_dev, y_dev: nrhs x N_A.
+ * Asynchronous on stream.  Errors: INVALID_ARG, CUDA. */
+cpm_status cpm_op_apply(const oras_precond* pc, const double* x_dev, double* y_dev, int nrhs,
+                        void* stream);
+
+/* z = M^{-1} r (Eq. algRAS): restrict r to every Sigma_j (zero on boundary unknowns),
+ * solve with the resident LU factors, write each disjoint set's values to z (restricted
+ * partition of unity).  FP64 in and out; the solves run in the factor precision.
+ * Asynchronous on stream.  Errors: INVALID_ARG, CUDA; device-side wait timeouts are
+ * reported by oras_check_status / cpm_gmres_solve. */
+cpm_status oras_apply(const oras_precond* pc, const double* r_dev, double* z_dev, int nrhs,
+                      void* stream);
+/* Synchronises the stream and reports device-side errors latched by earlier launches
+ * (TIMEOUT from a bounded wait), clearing them. */
+cpm_status oras_check_status(const oras_precond* pc, void* stream);
+
+typedef struct {
+  int restart;     /* m, default 50 */
+  double tol;      /* relative residual target ||f - A u|| <= tol ||f|| */
+  int max_it;      /* total inner iterations */
+  int use_graph;   /* 1: replay one captured iteration as a CUDA graph */
+  int zero_guess;  /* 1: u starts at 0; 0: u_dev holds the initial guess */
+} cpm_gmres_opts;
+
+typedef struct {
+  int iterations;
+  double relres;   /* true relative residual at exit */
+  int status;      /* cpm_status for this right-hand side */
+} cpm_gmres_result;
+
+/* Right-preconditioned flexible GMRES(m) with classical Gram-Schmidt applied twice, Givens
+ * rotations, FP64 Arnoldi (Sec. 2.2: (O)RAS embedded in GMRES).  Solves A u = f for each of
+ * nrhs right-hand sides; results[] has nrhs entries.  Returns CPM_OK only if every
+ * right-hand side converged, else the first failing status. */
+cpm_status cpm_gmres_solve(const oras_precond* pc, const double* f_dev, double* u_dev, int nrhs,
+                           const cpm_gmres_opts* opts, cpm_gmres_result* results, void* stream);
+
+void oras_destroy(oras_precond* pc);
+
+const char* cpm_status_string(cpm_status s);
+const char* cpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPM_H */

@@ -1,0 +1,238 @@
+"""GB300-native RAS/ORAS-preconditioned FGMRES for the closest point method.
+
+Python binding of the C ABI in include/cpm.h (method: May, Haynes & Ruuth,
+arXiv:1909.08734).  The functions below only marshal arguments: device vectors are torch
+CUDA tensors (FP64, contiguous), streams are torch.cuda.Stream objects (or None), and every
+computation runs in the library's own CUDA kernels.  Importing this package does not touch
+the GPU; the first call loads ``libcpm_gb300.so`` and raises if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _capi
+from ._capi import (CPM_BF16, CPM_FP32, CPM_FP64, CPM_ORAS, CPM_ORAS_R3, CPM_RAS,  # noqa: F401
+                    CPM_SET_BC_A, CPM_SET_BC_G, CPM_SET_BC_GEN, CPM_SET_BC_NEARX, CPM_SET_GHOST,
+                    CPM_SET_LAST, CPM_SET_OWN, CPM_SET_SIGMA, CPM_SPHERE, CPM_TORUS)
+
+PRECISIONS = {"fp64": CPM_FP64, "fp32": CPM_FP32, "bf16": CPM_BF16}
+TRANSMISSIONS = {"ras": CPM_RAS, "oras": CPM_ORAS, "oras_r3": CPM_ORAS_R3}
+SURFACES = {"sphere": CPM_SPHERE, "torus": CPM_TORUS}
+
+
+class CpmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _capi.load()
+        self.status = status
+        name = lib.cpm_status_string(status).decode()
+        msg = lib.cpm_last_error().decode()
+        super().__init__(f"{where}: {name}: {msg}")
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise CpmError(st, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, n: int, name: str):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} entries, needs {n}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Band:
+    def __init__(self, handle):
+        self._h = handle
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _capi.load().cpm_band_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = _capi.cpm_band_info()
+        _check(_capi.load().cpm_band_info_get(self._h, C.byref(inf)), "cpm_band_info_get")
+        n = inf.n_active + inf.n_ghost
+        arr = lambda p, cnt, dt: np.ctypeslib.as_array(p, shape=(cnt,)).astype(dt, copy=True)  # noqa: E731
+        return {
+            "n_active": inf.n_active, "n_ghost": inf.n_ghost, "p": inf.p, "h": inf.h,
+            "lambda": inf.lambda_,
+            "ijk": arr(inf.ijk, 3 * n, np.int64).reshape(n, 3),
+            "cp": arr(inf.cp, 3 * n, np.float64).reshape(n, 3),
+            "nbr": arr(inf.nbr, 6 * inf.n_active, np.int64).reshape(inf.n_active, 6),
+            "base": arr(inf.base, 3 * n, np.int64).reshape(n, 3),
+        }
+
+
+class Partition:
+    def __init__(self, handle, band: Band, n_sub: int):
+        self._h = handle
+        self.band = band          # keeps the band alive
+        self.n_sub = n_sub
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _capi.load().cpm_partition_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def labels(self) -> np.ndarray:
+        p = C.POINTER(C.c_int32)()
+        _check(_capi.load().cpm_partition_labels(self._h, C.byref(p)), "cpm_partition_labels")
+        n = self.band.info()["n_active"]
+        return np.ctypeslib.as_array(p, shape=(n,)).astype(np.int64)
+
+    def set(self, j: int, which: int) -> np.ndarray:
+        p = C.POINTER(C.c_int32)()
+        n = C.c_int64()
+        _check(_capi.load().cpm_partition_set(self._h, j, which, C.byref(p), C.byref(n)),
+               "cpm_partition_set")
+        if n.value == 0:
+            return np.zeros(0, dtype=np.int64)
+        return np.ctypeslib.as_array(p, shape=(n.value,)).astype(np.int64)
+
+    def cross_points(self) -> np.ndarray:
+        p = C.POINTER(C.c_int32)()
+        n = C.c_int64()
+        _check(_capi.load().cpm_partition_cross_points(self._h, C.byref(p), C.byref(n)),
+               "cpm_partition_cross_points")
+        if n.value == 0:
+            return np.zeros(0, dtype=np.int64)
+        return np.ctypeslib.as_array(p, shape=(n.value,)).astype(np.int64)
+
+
+class Preconditioner:
+    def __init__(self, handle, band: Band, part: Partition):
+        self._h = handle
+        self.band = band
+        self.part = part
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _capi.load().oras_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = _capi.oras_info()
+        _check(_capi.load().oras_info_get(self._h, C.byref(inf)), "oras_info_get")
+        return {f: getattr(inf, f) for f, _ in _capi.oras_info._fields_}
+
+    def local_sizes(self) -> np.ndarray:
+        out = np.zeros(self.part.n_sub, dtype=np.int64)
+        _check(_capi.load().oras_local_sizes(self._h, out.ctypes.data_as(C.c_void_p)), "oras_local_sizes")
+        return out
+
+    @property
+    def n_active(self) -> int:
+        return self.info()["n_active"]
+
+
+# ---------------------------------------------------------------- entry points
+def cpm_build_band(surface: str, R: float, r: float, h: float, p: int,
+                   lambda_over_h: float = 0.0) -> Band:
+    s = _capi.cpm_surface(SURFACES[surface], float(R), float(r))
+    h_out = C.c_void_p()
+    _check(_capi.load().cpm_build_band(C.byref(s), float(h), int(p), float(lambda_over_h),
+                                       C.byref(h_out)), "cpm_build_band")
+    return Band(h_out)
+
+
+def cpm_partition(band: Band, n_sub: int, leaf_weights=None, n_overlap: int = 2,
+                  align_passes: int = 0) -> Partition:
+    lib = _capi.load()
+    wptr = None
+    if leaf_weights is not None:
+        w = np.ascontiguousarray(leaf_weights, dtype=np.int64)
+        if len(w) != n_sub:
+            raise ValueError("leaf_weights must have n_sub entries")
+        wptr = w.ctypes.data_as(C.POINTER(C.c_int64))
+    h_out = C.c_void_p()
+    _check(lib.cpm_partition(band.handle, int(n_sub), wptr, int(n_overlap), int(align_passes),
+                             C.byref(h_out)), "cpm_partition")
+    return Partition(h_out, band, n_sub)
+
+
+def cpm_local_coo(band: Band, part: Partition, c: float, transmission: str, alpha: float,
+                  alpha_x: float, j: int):
+    lib = _capi.load()
+    n = C.c_int64()
+    nnz = C.c_int64()
+    tr = TRANSMISSIONS[transmission]
+    _check(lib.cpm_local_coo(band.handle, part.handle, float(c), tr, float(alpha), float(alpha_x),
+                             int(j), C.byref(n), C.byref(nnz), None, None, None), "cpm_local_coo")
+    rows = np.zeros(nnz.value, np.int32)
+    cols = np.zeros(nnz.value, np.int32)
+    vals = np.zeros(nnz.value, np.float64)
+    _check(lib.cpm_local_coo(band.handle, part.handle, float(c), tr, float(alpha), float(alpha_x),
+                             int(j), C.byref(n), C.byref(nnz), rows.ctypes.data_as(C.c_void_p),
+                             cols.ctypes.data_as(C.c_void_p), vals.ctypes.data_as(C.c_void_p)),
+           "cpm_local_coo")
+    return n.value, rows, cols, vals
+
+
+def oras_setup(band: Band, part: Partition, c: float, transmission: str = "oras",
+               alpha: float = 4.0, alpha_x: float = 40.0, precision: str = "fp64",
+               stream=None) -> Preconditioner:
+    h_out = C.c_void_p()
+    _check(_capi.load().oras_setup(band.handle, part.handle, float(c), TRANSMISSIONS[transmission],
+                                   float(alpha), float(alpha_x), PRECISIONS[precision],
+                                   _stream_ptr(stream), C.byref(h_out)), "oras_setup")
+    return Preconditioner(h_out, band, part)
+
+
+def cpm_op_apply(pc: Preconditioner, x, y, nrhs: int = 1, stream=None):
+    n = pc.n_active * nrhs
+    _check(_capi.load().cpm_op_apply(pc.handle, _dev_ptr(x, n, "x"), _dev_ptr(y, n, "y"), int(nrhs),
+                                     _stream_ptr(stream)), "cpm_op_apply")
+
+
+def oras_apply(pc: Preconditioner, r, z, nrhs: int = 1, stream=None):
+    n = pc.n_active * nrhs
+    _check(_capi.load().oras_apply(pc.handle, _dev_ptr(r, n, "r"), _dev_ptr(z, n, "z"), int(nrhs),
+                                   _stream_ptr(stream)), "oras_apply")
+
+
+def oras_check_status(pc: Preconditioner, stream=None):
+    _check(_capi.load().oras_check_status(pc.handle, _stream_ptr(stream)), "oras_check_status")
+
+
+def cpm_gmres_solve(pc: Preconditioner, f, u, nrhs: int = 1, restart: int = 50, tol: float = 1e-8,
+                    max_it: int = 1000, use_graph: bool = True, zero_guess: bool = True,
+                    stream=None, raise_on_failure: bool = True):
+    """Returns a list of dicts (iterations, relres, status) per right-hand side."""
+    n = pc.n_active * nrhs
+    opts = _capi.cpm_gmres_opts(int(restart), float(tol), int(max_it), int(bool(use_graph)),
+                                int(bool(zero_guess)))
+    res = (_capi.cpm_gmres_result * nrhs)()
+    st = _capi.load().cpm_gmres_solve(pc.handle, _dev_ptr(f, n, "f"), _dev_ptr(u, n, "u"), int(nrhs),
+                                      C.byref(opts), res, _stream_ptr(stream))
+    out = [{"iterations": r.iterations, "relres": r.relres, "status": r.status} for r in res]
+    if st != 0 and (raise_on_failure or st not in (_capi.CPM_ERR_NOT_CONVERGED,)):
+        raise CpmError(st, "cpm_gmres_solve")
+    return out
+
+
+def status_string(code: int) -> str:
+    return _capi.load().cpm_status_string(int(code)).decode()

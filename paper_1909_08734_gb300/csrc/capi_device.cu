@@ -1,0 +1,645 @@
+// C ABI: entry points that run on the GPU (preconditioner setup, operator apply,
+// preconditioner apply, FGMRES).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "cuda/kernels.h"
+#include "host/cpm_internal.h"
+
+using namespace cpmdev;
+
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+cpm_status cuda_fail(cudaError_t e, const char* where) {
+  cpm::set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? CPM_ERR_OOM : CPM_ERR_CUDA;
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e__ = (call);                         \
+    if (e__ != cudaSuccess) return cuda_fail(e__, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t upload(const std::vector<T>& v, void** d) {
+  *d = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(d, v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+void cpm::band_release_device(cpm::Band& b) {
+  if (b.d_device < 0) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(b.d_device);
+  cudaFree(b.d_pencil);
+  cudaFree(b.d_wts);
+  cudaFree(b.d_nbr);
+  cudaSetDevice(cur);
+  b.d_pencil = b.d_wts = b.d_nbr = nullptr;
+  b.d_device = -1;
+}
+
+struct oras_precond {
+  const cpm::Band* band = nullptr;
+  int device = -1;
+  int n_sub = 0, precision = 0, transmission = 0, t_max = 0;
+  double c = 0;
+  int64_t n_active = 0, n_nodes = 0;
+  std::vector<int64_t> n_local, n_sigma;
+  std::vector<SubMeta> meta;
+  int64_t sum_n = 0, sum_n2 = 0, sum_sigma = 0, rows_total = 0, tiles_total = 0;
+  double ms_assemble = 0, ms_factor = 0;
+  std::vector<DevBuf> bufs;
+  size_t device_bytes = 0, factor_bytes = 0;
+  // device pointers
+  void* tiles = nullptr;      // factors used by the solves
+  void* dinv = nullptr;
+  SubMeta* d_meta = nullptr;
+  int32_t* gather = nullptr;
+  int32_t* scatter = nullptr;
+  int* status = nullptr;
+  TrsvDev trsv{};
+  OperatorDev op{};
+  double* v_scratch = nullptr;     // extension values for cpm_op_apply (nrhs x N)
+  int64_t v_scratch_rhs = 0;
+  double* g_vext = nullptr;        // extension values owned by the FGMRES path
+  // FGMRES workspace
+  int g_m = 0;
+  GmresDev gm{};
+  double* g_state_host = nullptr;
+  int* g_istate_host = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t iter_graph = nullptr;
+  int graph_m = 0;
+
+  void* alloc(size_t bytes, cudaError_t* err) {
+    void* p = nullptr;
+    *err = cudaMalloc(&p, bytes ? bytes : 16);
+    if (*err == cudaSuccess) {
+      bufs.push_back({p, bytes});
+      device_bytes += bytes;
+    }
+    return p;
+  }
+  void release(void* p) {
+    for (size_t i = 0; i < bufs.size(); ++i)
+      if (bufs[i].p == p) {
+        cudaFree(p);
+        device_bytes -= bufs[i].bytes;
+        bufs.erase(bufs.begin() + i);
+        return;
+      }
+  }
+  ~oras_precond() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (device >= 0) cudaSetDevice(device);
+    if (iter_graph) cudaGraphExecDestroy(iter_graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (auto& b : bufs) cudaFree(b.p);
+    if (g_state_host) cudaFreeHost(g_state_host);
+    if (g_istate_host) cudaFreeHost(g_istate_host);
+    if (cur >= 0) cudaSetDevice(cur);
+  }
+};
+
+#define ALLOC(ptr, type, count)                                            \
+  do {                                                                     \
+    cudaError_t e__;                                                       \
+    ptr = (type*)pc->alloc(sizeof(type) * (size_t)(count), &e__);          \
+    if (e__ != cudaSuccess) return cuda_fail(e__, "cudaMalloc " #ptr);     \
+  } while (0)
+
+namespace {
+
+cpm_status ensure_band_on_device(const cpm::Band& B, int dev) {
+  if (B.d_device == dev) return CPM_OK;
+  if (B.d_device >= 0) cpm::band_release_device(const_cast<cpm::Band&>(B));
+  CK(upload(B.pencil, &B.d_pencil));
+  CK(upload(B.wts, &B.d_wts));
+  CK(upload(B.nbr, &B.d_nbr));
+  B.d_device = dev;
+  return CPM_OK;
+}
+
+int sm_count(int dev) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition& P, double c,
+                      int transmission, double alpha, double alpha_x, int precision,
+                      cudaStream_t s) {
+  const int ns = P.n_sub;
+  pc->band = &B;
+  pc->n_sub = ns;
+  pc->c = c;
+  pc->precision = precision;
+  pc->transmission = transmission;
+  pc->n_active = B.n_active;
+  pc->n_nodes = B.n_nodes();
+  CK(cudaGetDevice(&pc->device));
+  cpm_status st = ensure_band_on_device(B, pc->device);
+  if (st != CPM_OK) return st;
+
+  // ---- host: local operators in coordinate form ----
+  std::vector<cpm::LocalCOO> coo(ns);
+  std::vector<cpm_status> sts(ns, CPM_OK);
+  std::vector<std::string> errs(ns);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < ns; ++j) {
+    try {
+      sts[j] = cpm::build_local_coo(B, P, c, transmission, alpha, alpha_x, j, coo[j]);
+      if (sts[j] != CPM_OK) errs[j] = cpm_last_error();
+    } catch (const std::bad_alloc&) {
+      sts[j] = CPM_ERR_OOM;
+      errs[j] = "out of host memory building local operators";
+    }
+  }
+  for (int j = 0; j < ns; ++j)
+    if (sts[j] != CPM_OK) {
+      cpm::set_error(errs[j]);
+      return sts[j];
+    }
+  pc->meta.resize(ns);
+  pc->n_local.resize(ns);
+  pc->n_sigma.resize(ns);
+  int64_t tile_off = 0, row_off = 0, nnz = 0;
+  int t_max = 0;
+  std::vector<int64_t> flag_off(ns);
+  int64_t flags_total = 0;
+  for (int j = 0; j < ns; ++j) {
+    const int64_t n = coo[j].n;
+    const int T = (int)((n + TILE - 1) / TILE);
+    SubMeta m{};
+    m.tile_off = tile_off;
+    m.row_off = row_off;
+    m.T = T;
+    m.n = (int32_t)n;
+    m.n_sigma = (int32_t)coo[j].n_sigma;
+    pc->meta[j] = m;
+    pc->n_local[j] = n;
+    pc->n_sigma[j] = coo[j].n_sigma;
+    tile_off += (int64_t)T * T * TILE_ELEMS;
+    row_off += (int64_t)T * TILE;
+    nnz += (int64_t)coo[j].val.size();
+    t_max = std::max(t_max, T);
+    pc->sum_n += n;
+    pc->sum_n2 += n * n;
+    pc->sum_sigma += coo[j].n_sigma;
+    flag_off[j] = flags_total;
+    flags_total += 2 * T;
+  }
+  pc->t_max = t_max;
+  pc->rows_total = row_off;
+  pc->tiles_total = tile_off / TILE_ELEMS;
+  const bool fp64 = precision == CPM_FP64;
+  const size_t wbytes = fp64 ? 8 : 4;
+
+  // element offsets of every entry in the tiled layout
+  std::vector<int64_t> h_off(nnz);
+  std::vector<double> h_val(nnz);
+  {
+    std::vector<int64_t> start(ns + 1, 0);
+    for (int j = 0; j < ns; ++j) start[j + 1] = start[j] + (int64_t)coo[j].val.size();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int j = 0; j < ns; ++j) {
+      const SubMeta& m = pc->meta[j];
+      const cpm::LocalCOO& L = coo[j];
+      for (size_t e = 0; e < L.val.size(); ++e) {
+        const int i = L.row[e], k = L.col[e];
+        const int64_t tb = m.tile_off + ((int64_t)(k >> 6) * m.T + (i >> 6)) * TILE_ELEMS;
+        h_off[start[j] + e] = tb + (fp64 ? off_plain(i & 63, k & 63) : off_sw32(i & 63, k & 63));
+        h_val[start[j] + e] = L.val[e];
+      }
+    }
+  }
+  // unknown -> global index, ownership flags
+  std::vector<int32_t> unknowns(pc->sum_n), own(pc->sum_n, 0);
+  std::vector<int64_t> unk_off(ns);
+  {
+    int64_t o = 0;
+    std::vector<uint8_t> mine(B.n_active, 0);
+    for (int j = 0; j < ns; ++j) {
+      const cpm::SubSets& S = P.subs[j];
+      unk_off[j] = o;
+      for (int32_t g : S.own) mine[g] = 1;
+      int64_t t = 0;
+      for (int32_t g : S.sigma) { unknowns[o + t] = g; own[o + t] = mine[g]; ++t; }
+      if (transmission != CPM_RAS)
+        for (int32_t g : S.bc_a) { unknowns[o + t] = g; own[o + t] = 0; ++t; }
+      for (int32_t g : S.own) mine[g] = 0;
+      o += pc->n_local[j];
+    }
+  }
+  coo.clear();
+  coo.shrink_to_fit();
+
+  // ---- device buffers ----
+  void* work;
+  {
+    cudaError_t e;
+    work = pc->alloc(wbytes * (size_t)tile_off, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc factor tiles");
+  }
+  int32_t* ipiv;
+  ALLOC(pc->d_meta, SubMeta, ns);
+  ALLOC(ipiv, int32_t, row_off);
+  ALLOC(pc->gather, int32_t, row_off);
+  ALLOC(pc->scatter, int32_t, row_off);
+  ALLOC(pc->status, int, 1);
+  void* dinv;
+  {
+    cudaError_t e;
+    dinv = pc->alloc(wbytes * (size_t)row_off, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc dinv");
+  }
+  pc->dinv = dinv;
+  int32_t *d_unk, *d_own;
+  int64_t *d_unk_off, *d_off;
+  double* d_val;
+  ALLOC(d_unk, int32_t, pc->sum_n);
+  ALLOC(d_own, int32_t, pc->sum_n);
+  ALLOC(d_unk_off, int64_t, ns);
+  ALLOC(d_off, int64_t, nnz);
+  ALLOC(d_val, double, nnz);
+  CK(cudaMemcpyAsync(pc->d_meta, pc->meta.data(), sizeof(SubMeta) * ns, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_unk, unknowns.data(), 4 * pc->sum_n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_own, own.data(), 4 * pc->sum_n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_unk_off, unk_off.data(), 8 * ns, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_off, h_off.data(), 8 * nnz, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_val, h_val.data(), 8 * nnz, cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(pc->status, 0, sizeof(int), s));
+
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&e2));
+  CK(cudaEventRecord(e0, s));
+  CK(cudaMemsetAsync(work, 0, wbytes * (size_t)tile_off, s));
+  CK(launch_pad_identity(work, fp64, pc->d_meta, ns, t_max, s));
+  CK(launch_scatter(work, fp64, d_off, d_val, nnz, s));
+  CK(cudaEventRecord(e1, s));
+  FactorDev f{work, pc->d_meta, ipiv, pc->status, ns, t_max, fp64 ? 1 : 0};
+  const int use_tc = 0;
+  for (int step = 0; step < t_max; ++step) CK(launch_lu_step(f, step, use_tc, s));
+  CK(launch_lu_finish(f, d_unk, d_unk_off, d_own, pc->gather, pc->scatter, dinv, s));
+  CK(cudaEventRecord(e2, s));
+  CK(cudaStreamSynchronize(s));
+  float ms1 = 0, ms2 = 0;
+  cudaEventElapsedTime(&ms1, e0, e1);
+  cudaEventElapsedTime(&ms2, e1, e2);
+  pc->ms_assemble = ms1;
+  pc->ms_factor = ms2;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  pc->release(d_off);
+  pc->release(d_val);
+  pc->release(d_unk);
+  pc->release(d_own);
+  pc->release(d_unk_off);
+  pc->release(ipiv);
+  int hst = 0;
+  CK(cudaMemcpy(&hst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (hst & ST_SINGULAR) {
+    cpm::set_error("oras_setup: zero pivot in a local LU factorisation");
+    return CPM_ERR_SINGULAR;
+  }
+  if (precision == CPM_BF16) {
+    cudaError_t e;
+    void* lp = pc->alloc(2 * (size_t)tile_off, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc bf16 factors");
+    CK(launch_pack_bf16((const float*)work, (__nv_bfloat16*)lp, pc->tiles_total, s));
+    CK(cudaStreamSynchronize(s));
+    pc->release(work);
+    pc->tiles = lp;
+    pc->factor_bytes = 2 * (size_t)tile_off;
+  } else {
+    pc->tiles = work;
+    pc->factor_bytes = wbytes * (size_t)tile_off;
+  }
+
+  // ---- persistent triangular-solve schedule ----
+  std::vector<int2> items;
+  for (int t = 0; t < t_max; ++t)
+    for (int j = 0; j < ns; ++j)
+      if (t < pc->meta[j].T) items.push_back(make_int2(j, t));
+  for (int t = 0; t < t_max; ++t)
+    for (int j = 0; j < ns; ++j)
+      if (t < pc->meta[j].T) items.push_back(make_int2(j, (pc->meta[j].T - 1 - t) | (1 << 30)));
+  int2* d_items;
+  uint32_t *d_flags, *d_sync;
+  int64_t* d_flag_off;
+  ALLOC(d_items, int2, items.size());
+  ALLOC(d_flags, uint32_t, flags_total);
+  ALLOC(d_sync, uint32_t, 4);
+  ALLOC(d_flag_off, int64_t, ns);
+  void* ybuf;
+  {
+    cudaError_t e;
+    ybuf = pc->alloc(wbytes * (size_t)row_off, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc solve scratch");
+  }
+  CK(cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_flag_off, flag_off.data(), 8 * ns, cudaMemcpyHostToDevice));
+  CK(cudaMemset(d_flags, 0, 4 * flags_total));
+  CK(cudaMemset(d_sync, 0, 16));
+  TrsvDev& t = pc->trsv;
+  t.tiles = pc->tiles;
+  t.dinv = dinv;
+  t.meta = pc->d_meta;
+  t.gather = pc->gather;
+  t.scatter = pc->scatter;
+  t.items = d_items;
+  t.n_items = (int)items.size();
+  t.y = ybuf;
+  t.flags = d_flags;
+  t.flag_off = d_flag_off;
+  t.sync = d_sync;
+  t.status = pc->status;
+  t.precision = precision;
+  t.grid = sm_count(pc->device) * trsv_ctas_per_sm(precision);
+  CK(trsv_prepare(precision));
+
+  // ---- operator ----
+  OperatorDev& op = pc->op;
+  op.pencil = (const int32_t*)B.d_pencil;
+  op.wts = (const double*)B.d_wts;
+  op.nbr = (const int32_t*)B.d_nbr;
+  op.n_active = B.n_active;
+  op.n_nodes = B.n_nodes();
+  op.P = B.P();
+  op.diag = c + 6.0 / (B.h * B.h);
+  op.invh2 = 1.0 / (B.h * B.h);
+  return CPM_OK;
+}
+
+cpm_status ensure_v_scratch(oras_precond* pc, int nrhs) {
+  if (pc->v_scratch_rhs >= nrhs) return CPM_OK;
+  if (pc->v_scratch) pc->release(pc->v_scratch);
+  pc->v_scratch = nullptr;
+  pc->v_scratch_rhs = 0;
+  ALLOC(pc->v_scratch, double, (int64_t)nrhs * pc->n_nodes);
+  pc->v_scratch_rhs = nrhs;
+  return CPM_OK;
+}
+
+cpm_status ensure_gmres(oras_precond* pc, int m) {
+  if (pc->g_m == m) return CPM_OK;
+  GmresDev& g = pc->gm;
+  for (void* p : {(void*)g.V, (void*)g.Z, (void*)g.w, (void*)g.r, (void*)g.part, (void*)g.st, (void*)g.ist})
+    if (p) pc->release(p);
+  if (pc->iter_graph) {
+    cudaGraphExecDestroy(pc->iter_graph);
+    pc->iter_graph = nullptr;
+  }
+  g = GmresDev{};
+  pc->g_m = 0;
+  const int64_t n = pc->n_active;
+  g.n = n;
+  g.m = m;
+  g.nblk = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  if (g.nblk < 1) g.nblk = 1;
+  ALLOC(g.V, double, (int64_t)(m + 1) * n);
+  ALLOC(g.Z, double, (int64_t)m * n);
+  ALLOC(g.w, double, n);
+  ALLOC(g.r, double, n);
+  ALLOC(g.part, double, (int64_t)g.nblk * (m + 2));
+  ALLOC(g.st, double, gmres_state_size(m));
+  ALLOC(g.ist, int, 8);
+  CK(cudaMemset(g.ist, 0, 8 * sizeof(int)));
+  if (!pc->g_istate_host) CK(cudaMallocHost(&pc->g_istate_host, 8 * sizeof(int)));
+  if (!pc->g_state_host) CK(cudaMallocHost(&pc->g_state_host, 8 * sizeof(double)));
+  pc->g_m = m;
+  if (!pc->g_vext) ALLOC(pc->g_vext, double, pc->n_nodes);
+  return CPM_OK;
+}
+
+// One FGMRES iteration: z_k = M^{-1} v_k, w = A z_k, CGS2, Givens.
+cpm_status launch_iteration(oras_precond* pc, cudaStream_t s) {
+  GmresDev& g = pc->gm;
+  const int* done = g.ist + 2;
+  IndirectVec vk{g.V, 0, g.ist, g.n, 0};
+  IndirectVec zk{g.Z, 0, g.ist, g.n, 0};
+  CK(launch_trsv(pc->trsv, vk, zk, done, s));
+  CK(launch_apply(pc->op, zk, pc->g_vext, nullptr, direct(g.w, 0), 1, 0, done, s));
+  CK(launch_cgs2_and_givens(g, s));
+  return CPM_OK;
+}
+
+cpm_status solve_one(oras_precond* pc, const double* f, double* u, const cpm_gmres_opts& o,
+                     cpm_gmres_result* res, cudaStream_t s) {
+  GmresDev& g = pc->gm;
+  if (o.zero_guess) CK(cudaMemsetAsync(u, 0, sizeof(double) * g.n, s));
+  CK(launch_gmres_begin(g, f, o.tol, o.max_it, s));
+  CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(g.r, 0), 1, 1, nullptr, s));
+  CK(launch_gmres_residual_check(g, s));
+  for (;;) {
+    CK(cudaMemcpyAsync(pc->g_istate_host, g.ist, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (pc->g_istate_host[3] != -1) break;     // converged or failed
+    for (int it = 0; it < g.m; ++it) {
+      if (pc->iter_graph) CK(cudaGraphLaunch(pc->iter_graph, s));
+      else {
+        cpm_status st = launch_iteration(pc, s);
+        if (st != CPM_OK) return st;
+      }
+    }
+    CK(launch_gmres_restart_update(g, u, s));
+    CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(g.r, 0), 1, 1, nullptr, s));
+    CK(launch_gmres_residual_check(g, s));
+  }
+  CK(cudaMemcpy(pc->g_state_host, g.st + gmres_scalar_offset(g.m), 8 * sizeof(double),
+                cudaMemcpyDeviceToHost));
+  int dst = 0;
+  CK(cudaMemcpy(&dst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
+  res->iterations = pc->g_istate_host[1];
+  res->relres = pc->g_state_host[4];
+  res->status = pc->g_istate_host[3];
+  if (dst & ST_TIMEOUT) {
+    CK(cudaMemset(pc->status, 0, sizeof(int)));
+    res->status = CPM_ERR_TIMEOUT;
+  }
+  return CPM_OK;
+}
+
+cpm_status capture_graph(oras_precond* pc) {
+  if (!pc->cap_stream) CK(cudaStreamCreateWithFlags(&pc->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(pc->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cpm_status st = launch_iteration(pc, pc->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(pc->cap_stream, &graph);
+  if (st != CPM_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&pc->iter_graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  pc->graph_m = pc->g_m;
+  return CPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cpm_status oras_setup(const cpm_band* band, const cpm_part* part, double c, int transmission,
+                      double alpha, double alpha_x, int precision, void* stream, oras_precond** out) {
+  if (!band || !part || !out || part->p.band != &band->b) {
+    cpm::set_error("oras_setup: NULL argument or partition built from another band");
+    return CPM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (!(c > 0.0) || (precision != CPM_FP64 && precision != CPM_FP32 && precision != CPM_BF16) ||
+      (transmission != CPM_RAS && transmission != CPM_ORAS && transmission != CPM_ORAS_R3) ||
+      (transmission != CPM_RAS && !(alpha >= 0.0 && alpha_x >= 0.0))) {
+    cpm::set_error("oras_setup: need c > 0, a known precision / transmission, alpha >= 0");
+    return CPM_ERR_INVALID_ARG;
+  }
+  oras_precond* pc = nullptr;
+  try {
+    pc = new oras_precond();
+    cpm_status st = setup_impl(pc, band->b, part->p, c, transmission, alpha, alpha_x, precision,
+                               (cudaStream_t)stream);
+    if (st != CPM_OK) {
+      delete pc;
+      return st;
+    }
+  } catch (const std::bad_alloc&) {
+    delete pc;
+    cpm::set_error("oras_setup: out of host memory");
+    return CPM_ERR_OOM;
+  }
+  *out = pc;
+  return CPM_OK;
+}
+
+cpm_status oras_info_get(const oras_precond* pc, oras_info* o) {
+  if (!pc || !o) {
+    cpm::set_error("oras_info_get: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  o->n_sub = pc->n_sub;
+  o->n_active = pc->n_active;
+  o->n_nodes = pc->n_nodes;
+  o->precision = pc->precision;
+  o->transmission = pc->transmission;
+  o->max_n = pc->n_local.empty() ? 0 : *std::max_element(pc->n_local.begin(), pc->n_local.end());
+  o->sum_n = pc->sum_n;
+  o->sum_n2 = pc->sum_n2;
+  o->sum_sigma = pc->sum_sigma;
+  o->factor_bytes = (int64_t)pc->factor_bytes;
+  o->device_bytes = (int64_t)pc->device_bytes;
+  o->setup_ms_assemble = pc->ms_assemble;
+  o->setup_ms_factor = pc->ms_factor;
+  return CPM_OK;
+}
+
+cpm_status oras_local_sizes(const oras_precond* pc, int64_t* n_out) {
+  if (!pc || !n_out) {
+    cpm::set_error("oras_local_sizes: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  for (int j = 0; j < pc->n_sub; ++j) n_out[j] = pc->n_local[j];
+  return CPM_OK;
+}
+
+cpm_status cpm_op_apply(const oras_precond* cpc, const double* x_dev, double* y_dev, int nrhs,
+                        void* stream) {
+  oras_precond* pc = const_cast<oras_precond*>(cpc);
+  if (!pc || !x_dev || !y_dev || nrhs < 1) {
+    cpm::set_error("cpm_op_apply: bad argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  cpm_status st = ensure_v_scratch(pc, nrhs);
+  if (st != CPM_OK) return st;
+  CK(launch_apply(pc->op, direct(const_cast<double*>(x_dev), pc->n_active), pc->v_scratch, nullptr,
+                  direct(y_dev, pc->n_active), nrhs, 0, nullptr, (cudaStream_t)stream));
+  return CPM_OK;
+}
+
+cpm_status oras_apply(const oras_precond* pc, const double* r_dev, double* z_dev, int nrhs,
+                      void* stream) {
+  if (!pc || !r_dev || !z_dev || nrhs < 1) {
+    cpm::set_error("oras_apply: bad argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < nrhs; ++i)
+    CK(launch_trsv(pc->trsv, direct(const_cast<double*>(r_dev) + (int64_t)i * pc->n_active, 0),
+                   direct(z_dev + (int64_t)i * pc->n_active, 0), nullptr, (cudaStream_t)stream));
+  return CPM_OK;
+}
+
+cpm_status oras_check_status(const oras_precond* pc, void* stream) {
+  if (!pc) {
+    cpm::set_error("oras_check_status: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  int h = 0;
+  CK(cudaMemcpy(&h, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(pc->status, 0, sizeof(int)));
+  if (h & ST_TIMEOUT) {
+    cpm::set_error("a bounded device-side wait gave up");
+    return CPM_ERR_TIMEOUT;
+  }
+  return CPM_OK;
+}
+
+cpm_status cpm_gmres_solve(const oras_precond* cpc, const double* f_dev, double* u_dev, int nrhs,
+                           const cpm_gmres_opts* opts, cpm_gmres_result* results, void* stream) {
+  oras_precond* pc = const_cast<oras_precond*>(cpc);
+  if (!pc || !f_dev || !u_dev || nrhs < 1 || !results) {
+    cpm::set_error("cpm_gmres_solve: bad argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  cpm_gmres_opts o{50, 1e-8, 1000, 1, 1};
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > 128 || !(o.tol > 0.0) || o.max_it < 1) {
+    cpm::set_error("cpm_gmres_solve: need 1 <= restart <= 128, tol > 0, max_it >= 1");
+    return CPM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  cpm_status st = ensure_gmres(pc, o.restart);
+  if (st != CPM_OK) return st;
+  if (o.use_graph && !pc->iter_graph) {
+    st = capture_graph(pc);
+    if (st != CPM_OK) return st;
+  }
+  const bool had_graph = pc->iter_graph != nullptr;
+  cudaGraphExec_t saved = pc->iter_graph;
+  if (!o.use_graph) pc->iter_graph = nullptr;
+  cpm_status first = CPM_OK;
+  for (int i = 0; i < nrhs; ++i) {
+    st = solve_one(pc, f_dev + (int64_t)i * pc->n_active, u_dev + (int64_t)i * pc->n_active, o,
+                   &results[i], s);
+    if (st != CPM_OK) {
+      if (had_graph) pc->iter_graph = saved;
+      return st;
+    }
+    if (first == CPM_OK && results[i].status != CPM_OK) first = (cpm_status)results[i].status;
+  }
+  if (had_graph) pc->iter_graph = saved;
+  if (first != CPM_OK) cpm::set_error(std::string("cpm_gmres_solve: ") + cpm_status_string(first));
+  return first;
+}
+
+void oras_destroy(oras_precond* pc) { delete pc; }
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// C ABI: host-only entry points (band, partition, local operators, status strings).
+#include <new>
+#include <string>
+
+#include "host/cpm_internal.h"
+
+
+namespace cpm {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace cpm
+
+extern "C" {
+
+const char* cpm_last_error(void) { return cpm::g_err.c_str(); }
+
+const char* cpm_status_string(cpm_status s) {
+  switch (s) {
+    case CPM_OK: return "CPM_OK";
+    case CPM_ERR_INVALID_ARG: return "CPM_ERR_INVALID_ARG";
+    case CPM_ERR_OOM: return "CPM_ERR_OOM";
+    case CPM_ERR_CUDA: return "CPM_ERR_CUDA";
+    case CPM_ERR_SINGULAR: return "CPM_ERR_SINGULAR";
+    case CPM_ERR_NOT_CONVERGED: return "CPM_ERR_NOT_CONVERGED";
+    case CPM_ERR_BREAKDOWN: return "CPM_ERR_BREAKDOWN";
+    case CPM_ERR_NAN: return "CPM_ERR_NAN";
+    case CPM_ERR_TIMEOUT: return "CPM_ERR_TIMEOUT";
+    case CPM_ERR_BUDGET: return "CPM_ERR_BUDGET";
+    case CPM_ERR_STENCIL: return "CPM_ERR_STENCIL";
+  }
+  return "CPM_ERR_UNKNOWN";
+}
+
+cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
+                          cpm_band** out) {
+  if (!surface || !out) {
+    cpm::set_error("cpm_build_band: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    cpm_band* b = new cpm_band();
+    cpm::Surface s{surface->kind, surface->R, surface->r};
+    cpm_status st = cpm::build_band(s, h, p, lambda_over_h, b->b);
+    if (st != CPM_OK) {
+      delete b;
+      return st;
+    }
+    *out = b;
+    return CPM_OK;
+  } catch (const std::bad_alloc&) {
+    cpm::set_error("cpm_build_band: out of host memory");
+    return CPM_ERR_OOM;
+  }
+}
+
+cpm_status cpm_band_info_get(const cpm_band* band, cpm_band_info* out) {
+  if (!band || !out) {
+    cpm::set_error("cpm_band_info_get: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  const cpm::Band& B = band->b;
+  out->n_active = B.n_active;
+  out->n_ghost = B.n_ghost;
+  out->p = B.p;
+  out->h = B.h;
+  out->lambda = B.lam;
+  out->ijk = B.ijk.data();
+  out->cp = B.cp.data();
+  out->nbr = B.nbr.data();
+  out->base = B.base.data();
+  return CPM_OK;
+}
+
+void cpm_band_destroy(cpm_band* band) {
+  if (!band) return;
+  cpm::band_release_device(band->b);
+  delete band;
+}
+
+cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
+                         int n_overlap, int align_passes, cpm_part** out) {
+  if (!band || !out) {
+    cpm::set_error("cpm_partition: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (align_passes != 0) {
+    cpm::set_error("cpm_partition: interface alignment passes are not supported (use 0)");
+    return CPM_ERR_INVALID_ARG;
+  }
+  try {
+    cpm_part* p = new cpm_part();
+    cpm_status st = cpm::build_partition(band->b, n_sub, leaf_weights, n_overlap, p->p);
+    if (st != CPM_OK) {
+      delete p;
+      return st;
+    }
+    *out = p;
+    return CPM_OK;
+  } catch (const std::bad_alloc&) {
+    cpm::set_error("cpm_partition: out of host memory");
+    return CPM_ERR_OOM;
+  }
+}
+
+cpm_status cpm_partition_labels(const cpm_part* part, const int32_t** labels) {
+  if (!part || !labels) {
+    cpm::set_error("cpm_partition_labels: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  *labels = part->p.labels.data();
+  return CPM_OK;
+}
+
+cpm_status cpm_partition_set(const cpm_part* part, int j, int which, const int32_t** data,
+                             int64_t* len) {
+  if (!part || !data || !len || j < 0 || j >= part->p.n_sub) {
+    cpm::set_error("cpm_partition_set: bad argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  const cpm::SubSets& S = part->p.subs[j];
+  const std::vector<int32_t>* v = nullptr;
+  switch (which) {
+    case CPM_SET_OWN: v = &S.own; break;
+    case CPM_SET_SIGMA: v = &S.sigma; break;
+    case CPM_SET_LAST: v = &S.last; break;
+    case CPM_SET_GHOST: v = &S.ghost; break;
+    case CPM_SET_BC_A: v = &S.bc_a; break;
+    case CPM_SET_BC_G: v = &S.bc_g; break;
+    case CPM_SET_BC_GEN: v = &S.bc_gen; break;
+    case CPM_SET_BC_NEARX: v = &S.bc_nearx; break;
+    default:
+      cpm::set_error("cpm_partition_set: unknown set selector");
+      return CPM_ERR_INVALID_ARG;
+  }
+  *data = v->data();
+  *len = (int64_t)v->size();
+  return CPM_OK;
+}
+
+cpm_status cpm_partition_cross_points(const cpm_part* part, const int32_t** data,
+                                      int64_t* len) {
+  if (!part || !data || !len) {
+    cpm::set_error("cpm_partition_cross_points: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  *data = part->p.cross.data();
+  *len = (int64_t)part->p.cross.size();
+  return CPM_OK;
+}
+
+void cpm_partition_destroy(cpm_part* part) { delete part; }
+
+cpm_status cpm_local_coo(const cpm_band* band, const cpm_part* part, double c,
+                         int transmission, double alpha, double alpha_x, int j, int64_t* n,
+                         int64_t* nnz, int32_t* rows, int32_t* cols, double* vals) {
+  if (!band || !part || !n || !nnz) {
+    cpm::set_error("cpm_local_coo: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  try {
+    cpm::LocalCOO L;
+    cpm_status st = cpm::build_local_coo(band->b, part->p, c, transmission, alpha, alpha_x, j, L);
+    if (st != CPM_OK) return st;
+    *n = L.n;
+    if (rows && cols && vals) {
+      if (*nnz < (int64_t)L.val.size()) {
+        cpm::set_error("cpm_local_coo: output arrays too small");
+        return CPM_ERR_INVALID_ARG;
+      }
+      for (size_t t = 0; t < L.val.size(); ++t) {
+        rows[t] = L.row[t];
+        cols[t] = L.col[t];
+        vals[t] = L.val[t];
+      }
+    }
+    *nnz = (int64_t)L.val.size();
+    return CPM_OK;
+  } catch (const std::bad_alloc&) {
+    cpm::set_error("cpm_local_coo: out of host memory");
+    return CPM_ERR_OOM;
+  }
+}
+
+}  // extern "C"

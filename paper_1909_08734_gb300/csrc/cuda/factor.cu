@@ -1,0 +1,303 @@
+// Batched dense LU with partial pivoting of all local matrices A_j (Sec. 5: the local
+// problems are solved by LU factorisation).  Every A_j is padded to 64 T_j with an
+// identity block and stored as 64 x 64 tiles; one blocked right-looking step per tile
+// column s runs over all subdomains at once:
+//   panel  : factor tile column s (rows >= 64 s) column by column, pivoting on max |a|
+//   swap   : apply the panel's row interchanges to every other tile column
+//   trsm   : U_sJ = L_ss^{-1} A_sJ for J > s
+//   update : A_IJ -= L_Is U_sJ for I, J > s   (the dense contraction; SIMT here, the
+//            tensor-core version lives in lu_tc.cu)
+// FP64 mode keeps double tiles; FP32 and BF16 modes keep float tiles in the swizzled
+// layout of common.cuh.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cpmdev {
+
+template <typename T>
+__device__ __forceinline__ T& at(T* a, const SubMeta& m, int i, int j) {
+  return a[tile_base(m, i >> 6, j >> 6) + Layout<T>::off(i & 63, j & 63)];
+}
+template <typename T>
+__device__ __forceinline__ T at(const T* a, const SubMeta& m, int i, int j) {
+  return a[tile_base(m, i >> 6, j >> 6) + Layout<T>::off(i & 63, j & 63)];
+}
+
+// ---------------------------------------------------------------- assembly
+template <typename T>
+__global__ void scatter_kernel(T* a, const int64_t* __restrict__ off, const double* __restrict__ val,
+                               int64_t nnz) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    a[off[e]] = (T)val[e];
+}
+
+template <typename T>
+__global__ void pad_identity_kernel(T* a, const SubMeta* __restrict__ meta) {
+  const SubMeta m = meta[blockIdx.y];
+  const int np = 64 * m.T;
+  for (int i = m.n + blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
+    at(a, m, i, i) = (T)1;
+}
+
+cudaError_t launch_scatter(void* a, int fp64, const int64_t* off, const double* val, int64_t nnz,
+                           cudaStream_t s) {
+  if (nnz == 0) return cudaSuccess;
+  unsigned blocks = (unsigned)((nnz + 255) / 256);
+  if (blocks > 152u * 64u) blocks = 152u * 64u;
+  if (fp64) scatter_kernel<double><<<blocks, 256, 0, s>>>((double*)a, off, val, nnz);
+  else scatter_kernel<float><<<blocks, 256, 0, s>>>((float*)a, off, val, nnz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_identity(void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
+                                cudaStream_t s) {
+  dim3 g(1, n_sub);
+  if (fp64) pad_identity_kernel<double><<<g, 64, 0, s>>>((double*)a, meta);
+  else pad_identity_kernel<float><<<g, 64, 0, s>>>((float*)a, meta);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- panel
+constexpr int PANEL_THREADS = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(T* a, const SubMeta* __restrict__ meta,
+                                                                 int32_t* ipiv, int* status, int s) {
+  const SubMeta m = meta[blockIdx.x];
+  if (s >= m.T) return;
+  const int np = 64 * m.T, k0 = 64 * s, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  __shared__ T prow[64];
+  __shared__ double wv[PANEL_THREADS / 32];
+  __shared__ int wi[PANEL_THREADS / 32];
+  __shared__ int piv_sh;
+  for (int c = 0; c < 64; ++c) {
+    const int col = k0 + c;
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = col + tid; i < np; i += PANEL_THREADS) {
+      double v = fabs((double)at(a, m, i, col));
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { wv[warp] = best; wi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      best = wv[0]; bi = wi[0];
+      for (int w = 1; w < PANEL_THREADS / 32; ++w)
+        if (wv[w] > best || (wv[w] == best && wi[w] < bi)) { best = wv[w]; bi = wi[w]; }
+      if (!(best > 0.0)) {             // zero (or NaN) column: singular local matrix
+        atomicOr(status, ST_SINGULAR);
+        bi = col;
+      }
+      piv_sh = bi;
+      ipiv[m.row_off + col] = bi;
+    }
+    __syncthreads();
+    const int piv = piv_sh;
+    if (piv != col && tid < 64) {
+      T t0 = at(a, m, col, k0 + tid);
+      at(a, m, col, k0 + tid) = at(a, m, piv, k0 + tid);
+      at(a, m, piv, k0 + tid) = t0;
+    }
+    __syncthreads();
+    if (tid < 64) prow[tid] = at(a, m, col, k0 + tid);
+    __syncthreads();
+    const T d = prow[c];
+    const T inv = d != (T)0 ? (T)1 / d : (T)0;
+    for (int i = col + 1 + tid; i < np; i += PANEL_THREADS) {
+      T l = at(a, m, i, col) * inv;
+      at(a, m, i, col) = l;
+      for (int cc = c + 1; cc < 64; ++cc) at(a, m, i, k0 + cc) -= l * prow[cc];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- row interchanges
+template <typename T>
+__global__ void lu_swap_kernel(T* a, const SubMeta* __restrict__ meta, const int32_t* __restrict__ ipiv,
+                               int s) {
+  const SubMeta m = meta[blockIdx.y];
+  const int J = blockIdx.x;
+  if (s >= m.T || J >= m.T || J == s) return;
+  const int k0 = 64 * s, col = 64 * J + threadIdx.x;
+  for (int c = 0; c < 64; ++c) {
+    const int r = k0 + c, p = ipiv[m.row_off + r];
+    if (p != r) {
+      T t0 = at(a, m, r, col);
+      at(a, m, r, col) = at(a, m, p, col);
+      at(a, m, p, col) = t0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- U_sJ = L_ss^{-1} A_sJ
+template <typename T>
+__global__ void __launch_bounds__(64) lu_trsm_kernel(T* a, const SubMeta* __restrict__ meta, int s) {
+  const SubMeta m = meta[blockIdx.y];
+  const int J = s + 1 + blockIdx.x;
+  if (J >= m.T) return;
+  __shared__ T L[64][65];
+  const T* ts = a + tile_base(m, s, s);
+  for (int e = threadIdx.x; e < 4096; e += 64) {
+    int i = e & 63, j = e >> 6;
+    L[i][j] = ts[Layout<T>::off(i, j)];
+  }
+  __syncthreads();
+  T* tj = a + tile_base(m, s, J);
+  const int col = threadIdx.x;
+  T x[64];
+#pragma unroll
+  for (int r = 0; r < 64; ++r) x[r] = tj[Layout<T>::off(r, col)];
+#pragma unroll
+  for (int r = 1; r < 64; ++r) {
+    T acc = x[r];
+#pragma unroll
+    for (int c = 0; c < r; ++c) acc -= L[r][c] * x[c];
+    x[r] = acc;
+  }
+#pragma unroll
+  for (int r = 0; r < 64; ++r) tj[Layout<T>::off(r, col)] = x[r];
+}
+
+// ---------------------------------------------------------------- A_IJ -= L_Is U_sJ (SIMT)
+template <typename T>
+__global__ void __launch_bounds__(256) lu_update_simt_kernel(T* a, const SubMeta* __restrict__ meta,
+                                                             int s, int t_max) {
+  const SubMeta m = meta[blockIdx.y];
+  const int W = t_max - 1 - s;
+  const int I = s + 1 + blockIdx.x / W, J = s + 1 + blockIdx.x % W;
+  if (I >= m.T || J >= m.T) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* As = (T*)smem_raw;              // As[i*65 + k]
+  T* Bs = As + 64 * 65;              // Bs[k*65 + j]
+  const T* ta = a + tile_base(m, I, s);
+  const T* tb = a + tile_base(m, s, J);
+  for (int e = threadIdx.x; e < 4096; e += 256) {
+    int i = e & 63, k = e >> 6;
+    As[i * 65 + k] = ta[Layout<T>::off(i, k)];
+    Bs[i * 65 + k] = tb[Layout<T>::off(i, k)];   // (row i = k-index of U, col k = j)
+  }
+  __syncthreads();
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[p][q] = (T)0;
+#pragma unroll 8
+  for (int k = 0; k < 64; ++k) {
+    T av[4], bv[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) av[p] = As[(ti + 16 * p) * 65 + k];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bv[q] = Bs[k * 65 + tj + 16 * q];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] += av[p] * bv[q];
+  }
+  T* tc = a + tile_base(m, I, J);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) tc[Layout<T>::off(ti + 16 * p, tj + 16 * q)] -= acc[p][q];
+}
+
+
+
+cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_t s) {
+  const int W = f.t_max - 1 - step;
+  if (f.fp64) {
+    double* a = (double*)f.a;
+    lu_panel_kernel<double><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+    lu_swap_kernel<double><<<dim3(f.t_max, f.n_sub), 64, 0, s>>>(a, f.meta, f.ipiv, step);
+    if (W > 0) {
+      lu_trsm_kernel<double><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step);
+      size_t sm = 2 * 64 * 65 * sizeof(double);
+      cudaFuncSetAttribute(lu_update_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      lu_update_simt_kernel<double><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max);
+    }
+  } else {
+    float* a = (float*)f.a;
+    lu_panel_kernel<float><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+    lu_swap_kernel<float><<<dim3(f.t_max, f.n_sub), 64, 0, s>>>(a, f.meta, f.ipiv, step);
+    if (W > 0) {
+      lu_trsm_kernel<float><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step);
+      size_t sm = 2 * 64 * 65 * sizeof(float);
+      lu_update_simt_kernel<float><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max);
+    }
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- after the factorisation
+// perm: the row interchanges applied in order to the identity; gather[r] = global index of
+// local unknown perm[r] when it carries residual (first n_sigma unknowns), else -1;
+// scatter[r] = global index of local unknown r if r is in the disjoint set, else -1;
+// dinv[r] = 1 / U_rr.
+template <typename T>
+__global__ void lu_finish_kernel(const T* a, const SubMeta* __restrict__ meta, const int32_t* ipiv,
+                                 const int32_t* __restrict__ unknowns, const int64_t* __restrict__ unk_off,
+                                 const int32_t* __restrict__ own_flag, int32_t* gather,
+                                 int32_t* scatter, T* dinv) {
+  const SubMeta m = meta[blockIdx.x];
+  const int np = 64 * m.T;
+  int32_t* perm = gather + m.row_off;       // built in place, then mapped
+  if (threadIdx.x == 0) {
+    for (int r = 0; r < np; ++r) perm[r] = r;
+    for (int r = 0; r < np; ++r) {
+      int p = ipiv[m.row_off + r];
+      int t = perm[r]; perm[r] = perm[p]; perm[p] = t;
+    }
+  }
+  __syncthreads();
+  const int64_t uo = unk_off[blockIdx.x];
+  for (int r = threadIdx.x; r < np; r += blockDim.x) {
+    int pr = perm[r];
+    perm[r] = pr < m.n_sigma ? unknowns[uo + pr] : -1;
+    scatter[m.row_off + r] = (r < m.n && own_flag[uo + r]) ? unknowns[uo + r] : -1;
+    T d = at(a, m, r, r);
+    dinv[m.row_off + r] = d != (T)0 ? (T)1 / d : (T)0;
+  }
+}
+
+cudaError_t launch_lu_finish(const FactorDev& f, const int32_t* unknowns, const int64_t* unk_off,
+                             const int32_t* own_flag, int32_t* gather, int32_t* scatter,
+                             void* dinv, cudaStream_t s) {
+  if (f.fp64)
+    lu_finish_kernel<double><<<f.n_sub, 256, 0, s>>>((const double*)f.a, f.meta, f.ipiv, unknowns,
+                                                     unk_off, own_flag, gather, scatter, (double*)dinv);
+  else
+    lu_finish_kernel<float><<<f.n_sub, 256, 0, s>>>((const float*)f.a, f.meta, f.ipiv, unknowns,
+                                                    unk_off, own_flag, gather, scatter, (float*)dinv);
+  return cudaGetLastError();
+}
+
+__global__ void pack_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ out,
+                                 int64_t n_tiles) {
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const float* src = a + t * TILE_ELEMS;
+    __nv_bfloat16* dst = out + t * TILE_ELEMS;
+    for (int e = threadIdx.x; e < TILE_ELEMS; e += blockDim.x) {
+      int i = e & 63, j = e >> 6;
+      dst[off_plain(i, j)] = __float2bfloat16_rn(src[off_sw32(i, j)]);
+    }
+  }
+}
+
+cudaError_t launch_pack_bf16(const float* a, __nv_bfloat16* out, int64_t n_tiles, cudaStream_t s) {
+  unsigned g = (unsigned)(n_tiles < 152 * 16 ? n_tiles : 152 * 16);
+  if (g == 0) return cudaSuccess;
+  pack_bf16_kernel<<<g, 256, 0, s>>>(a, out, n_tiles);
+  return cudaGetLastError();
+}
+
+}  // namespace cpmdev

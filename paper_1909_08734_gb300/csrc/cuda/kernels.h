@@ -1,0 +1,101 @@
+// Launchers of the device kernels (host-callable), shared by the C ABI implementation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace cpmdev {
+
+// A vector whose address may depend on a device-resident index k (so that one captured
+// CUDA graph serves every Krylov step): ptr(r) = base + r*rhs_stride + (*k + k_add)*k_stride.
+struct IndirectVec {
+  double* base;
+  int64_t rhs_stride;
+  const int* k;
+  int64_t k_stride;
+  int k_add;
+  __device__ __forceinline__ double* ptr(int r) const {
+    int kk = k ? (*k + k_add) : 0;
+    return base + (int64_t)r * rhs_stride + (int64_t)kk * k_stride;
+  }
+};
+inline IndirectVec direct(double* p, int64_t rhs_stride) { return IndirectVec{p, rhs_stride, nullptr, 0, 0}; }
+
+struct OperatorDev {
+  const int32_t* pencil;   // N x P^2
+  const double* wts;       // N x 3 x P
+  const int32_t* nbr;      // N_A x 6
+  int64_t n_active, n_nodes;
+  int P;
+  double diag, invh2;
+};
+
+cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
+                         IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s);
+
+// ---- local factorisation ----
+struct FactorDev {
+  void* a;                 // working tiles (double for FP64, float otherwise)
+  const SubMeta* meta;     // n_sub records
+  int32_t* ipiv;           // per padded row: pivot row chosen at that step (local index)
+  int* status;             // device status word
+  int n_sub;
+  int t_max;
+  int fp64;                // 1: double tiles, 0: float (swizzled) tiles
+};
+cudaError_t launch_scatter(void* a, int fp64, const int64_t* off, const double* val, int64_t nnz,
+                           cudaStream_t s);
+cudaError_t launch_pad_identity(void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
+                                cudaStream_t s);
+cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_t s);
+cudaError_t launch_lu_finish(const FactorDev& f, const int32_t* unknowns, const int64_t* unk_off,
+                             const int32_t* own_flag, int32_t* gather, int32_t* scatter,
+                             void* dinv, cudaStream_t s);
+cudaError_t launch_pack_bf16(const float* a, __nv_bfloat16* out, int64_t n_tiles, cudaStream_t s);
+
+// ---- batched local solves ----
+struct TrsvDev {
+  const void* tiles;       // factor tiles (double / float swizzled / bf16)
+  const void* dinv;        // 1/U_ii per padded row (double for FP64, float otherwise)
+  const SubMeta* meta;
+  const int32_t* gather;   // per padded row: global active index of the permuted local row or -1
+  const int32_t* scatter;  // per padded row: global index if the unknown is owned, else -1
+  const int2* items;       // (subdomain, tile row | direction bit 30)
+  int n_items;
+  void* y;                 // per padded row scratch (compute precision)
+  uint32_t* flags;         // 2 per tile row: forward, backward
+  const int64_t* flag_off; // per subdomain offset into flags
+  uint32_t* sync;          // [0] item counter, [1] finished CTAs, [2] epoch, [3] abort
+  int* status;
+  int precision;           // 0 fp64, 1 fp32, 2 bf16
+  int grid;
+};
+cudaError_t launch_trsv(const TrsvDev& t, IndirectVec r_in, IndirectVec z_out, const int* done,
+                        cudaStream_t s);
+int trsv_ctas_per_sm(int precision);
+cudaError_t trsv_prepare(int precision);
+
+// ---- Krylov kernels ----
+struct GmresDev {
+  double* V;        // (m+1) x N
+  double* Z;        // m x N
+  double* w;        // N
+  double* r;        // N
+  double* part;     // partial sums [nblk][m+2]
+  double* st;       // state doubles: H, cs, sn, g, y, scalars
+  int* ist;         // state ints: [0] k, [1] total, [2] done, [3] status, [4] kdone, [5] max_it
+  int64_t n;
+  int m;
+  int nblk;
+};
+int gmres_state_size(int m);       // doubles of state for restart length m
+int gmres_scalar_offset(int m);     // offset of the scalars (||f||, tol, beta, ||w||, relres)
+cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, double tol, int max_it,
+                               cudaStream_t s);
+cudaError_t launch_cgs2_and_givens(const GmresDev& g, cudaStream_t s);
+cudaError_t launch_gmres_restart_update(const GmresDev& g, double* u, cudaStream_t s);
+cudaError_t launch_gmres_residual_check(const GmresDev& g, cudaStream_t s);
+
+}  // namespace cpmdev

@@ -1,0 +1,98 @@
+// Internal host-side structures of the CPM Schwarz library.
+// Host code is compiled with -ffp-contract=off so that every set-membership decision
+// (tube test, stencil bases, bisection order, argmins) is reproducible bit for bit.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../../include/cpm.h"
+
+namespace cpm {
+
+void set_error(const std::string& msg);
+
+struct Surface {
+  int kind;
+  double R, r;
+};
+
+// Closest point (Sec. 2.1). Returns false where CP is undefined (sphere centre, torus axis
+// or ring circle); such points are never band nodes.
+bool closest_point(const Surface& s, const double x[3], double y[3]);
+// Unit surface normal at a surface point y.
+void surface_normal(const Surface& s, const double y[3], double n[3]);
+
+// 1-D barycentric Lagrange weights on nodes 0..p at offset t (Sec. 2.1, second form).
+void bary_weights(double t, int p, double* w);
+// Stencil base (lowest node) and the 1-D weights of interpolation at point y.
+void point_weights(const double y[3], double h, int p, int32_t base[3], double* wx,
+                   double* wy, double* wz);
+
+struct Band {
+  Surface surf;
+  double h = 0, lam = 0;
+  int p = 0;
+  int64_t n_active = 0, n_ghost = 0;
+  std::vector<int32_t> ijk;      // (N) x 3
+  std::vector<double> cp;        // (N) x 3
+  std::vector<int32_t> nbr;      // N_A x 6
+  std::vector<int32_t> base;     // N x 3 stencil bases of CP(x)
+  std::vector<double> wts;       // N x 3 x (p+1) 1-D weights (x, then y, then z)
+  std::vector<int32_t> pencil;   // N x (p+1)^2 first active index of each z-pencil
+  int32_t lo[3] = {0, 0, 0}, dims[3] = {0, 0, 0};
+  std::vector<int32_t> grid;     // dense index grid, -1 = no node
+  int64_t n_nodes() const { return n_active + n_ghost; }
+  int32_t lookup(int64_t i, int64_t j, int64_t k) const {
+    int64_t a = i - lo[0], b = j - lo[1], c = k - lo[2];
+    if (a < 0 || b < 0 || c < 0 || a >= dims[0] || b >= dims[1] || c >= dims[2]) return -1;
+    return grid[(a * dims[1] + b) * dims[2] + c];
+  }
+  int P() const { return p + 1; }
+  // Device copies (uploaded lazily by oras_setup, freed with the band).
+  mutable void* d_pencil = nullptr;
+  mutable void* d_wts = nullptr;
+  mutable void* d_nbr = nullptr;
+  mutable int d_device = -1;
+};
+
+struct SubSets {
+  std::vector<int32_t> own, sigma, last, ghost, bc_a, bc_g;
+  std::vector<int32_t> bc_gen;    // generator (last-layer node) of CP_{S_j} per BC node
+  std::vector<int32_t> bc_nearx;  // 1 if the BC node is near a cross point
+};
+
+struct Partition {
+  const Band* band = nullptr;
+  int n_sub = 0, n_overlap = 0;
+  std::vector<int32_t> labels;
+  std::vector<int32_t> cross;
+  std::vector<SubSets> subs;
+};
+
+// Local operator of one subdomain as summed COO triplets.
+struct LocalCOO {
+  int64_t n = 0;          // local unknowns
+  int64_t n_sigma = 0;    // the first n_sigma are Sigma_j
+  std::vector<int32_t> row, col;
+  std::vector<double> val;
+};
+
+cpm_status build_band(const Surface& s, double h, int p, double lam_over_h, Band& out);
+// Frees the band's device copies (defined with the CUDA code).
+void band_release_device(Band& b);
+cpm_status build_partition(const Band& band, int n_sub, const int64_t* weights, int n_overlap,
+                           Partition& out);
+cpm_status build_local_coo(const Band& band, const Partition& part, double c, int transmission,
+                           double alpha, double alpha_x, int j, LocalCOO& out);
+
+}  // namespace cpm
+
+// Opaque handle types of the C ABI.
+struct cpm_band {
+  cpm::Band b;
+};
+struct cpm_part {
+  cpm::Partition p;
+};

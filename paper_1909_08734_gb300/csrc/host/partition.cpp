@@ -1,0 +1,249 @@
+// Disjoint split, overlap growth and node sets (Sec. 3.1, Sec. 4.1, Sec. 4.2, Sec. 5.2.2).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "cpm_internal.h"
+
+namespace cpm {
+
+namespace {
+
+// Recursive coordinate bisection on CP of the actives (stands in for the graph partitioner
+// of Sec. 3.1).  Axis of largest extent (ties x<y<z), order (CP[axis], index), left half
+// gets floor(n * W_left / W) points and leaves [l0, l0 + P/2).
+void rcb(const Band& B, const std::vector<int64_t>& w, std::vector<int32_t>& labels) {
+  struct Job {
+    std::vector<int32_t> idx;
+    int l0, l1;
+  };
+  std::vector<Job> stack;
+  Job root;
+  root.idx.resize(B.n_active);
+  std::iota(root.idx.begin(), root.idx.end(), 0);
+  root.l0 = 0;
+  root.l1 = (int)w.size();
+  stack.push_back(std::move(root));
+  while (!stack.empty()) {
+    Job job = std::move(stack.back());
+    stack.pop_back();
+    const int P = job.l1 - job.l0;
+    if (P == 1) {
+      for (int32_t g : job.idx) labels[g] = job.l0;
+      continue;
+    }
+    double mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) { mn[a] = mx[a] = B.cp[3 * (size_t)job.idx[0] + a]; }
+    for (int32_t g : job.idx)
+      for (int a = 0; a < 3; ++a) {
+        double v = B.cp[3 * (size_t)g + a];
+        mn[a] = std::min(mn[a], v);
+        mx[a] = std::max(mx[a], v);
+      }
+    double ext[3] = {mx[0] - mn[0], mx[1] - mn[1], mx[2] - mn[2]};
+    int axis = 0;
+    if (ext[1] > ext[axis]) axis = 1;
+    if (ext[2] > ext[axis]) axis = 2;
+    std::sort(job.idx.begin(), job.idx.end(), [&](int32_t a, int32_t b) {
+      double va = B.cp[3 * (size_t)a + axis], vb = B.cp[3 * (size_t)b + axis];
+      return va < vb || (va == vb && a < b);
+    });
+    const int PL = P / 2;
+    int64_t WL = 0, W = 0;
+    for (int l = job.l0; l < job.l1; ++l) {
+      W += w[l];
+      if (l < job.l0 + PL) WL += w[l];
+    }
+    const int64_t n = (int64_t)job.idx.size();
+    const int64_t nL = (n * WL) / W;
+    Job L, R;
+    L.idx.assign(job.idx.begin(), job.idx.begin() + nL);
+    R.idx.assign(job.idx.begin() + nL, job.idx.end());
+    L.l0 = job.l0; L.l1 = job.l0 + PL;
+    R.l0 = job.l0 + PL; R.l1 = job.l1;
+    stack.push_back(std::move(R));
+    stack.push_back(std::move(L));
+  }
+}
+
+void sort_unique(std::vector<int32_t>& v) {
+  std::sort(v.begin(), v.end());
+  v.erase(std::unique(v.begin(), v.end()), v.end());
+}
+
+}  // namespace
+
+cpm_status build_partition(const Band& B, int n_sub, const int64_t* weights, int n_overlap,
+                           Partition& part) {
+  if (n_sub < 1 || n_overlap < 0 || n_sub > B.n_active) {
+    set_error("cpm_partition: need 1 <= n_sub <= N_A and n_overlap >= 0");
+    return CPM_ERR_INVALID_ARG;
+  }
+  std::vector<int64_t> w(n_sub, 1);
+  if (weights)
+    for (int l = 0; l < n_sub; ++l) {
+      if (weights[l] <= 0) {
+        set_error("cpm_partition: leaf weights must be positive");
+        return CPM_ERR_INVALID_ARG;
+      }
+      w[l] = weights[l];
+    }
+  const int64_t na = B.n_active, N = B.n_nodes();
+  part = Partition();
+  part.band = &B;
+  part.n_sub = n_sub;
+  part.n_overlap = n_overlap;
+  part.labels.assign(na, -1);
+  rcb(B, w, part.labels);
+  std::vector<int64_t> count(n_sub, 0);
+  for (int64_t g = 0; g < na; ++g) count[part.labels[g]]++;
+  for (int l = 0; l < n_sub; ++l)
+    if (count[l] == 0) {
+      set_error("cpm_partition: a subdomain is empty");
+      return CPM_ERR_INVALID_ARG;
+    }
+  // cross-point nodes: active neighbours in >= 2 subdomains other than the own one
+  for (int64_t g = 0; g < na; ++g) {
+    int32_t seen[6];
+    int ns = 0;
+    for (int m = 0; m < 6; ++m) {
+      int32_t q = B.nbr[6 * g + m];
+      if (q >= na) continue;
+      int32_t l = part.labels[q];
+      if (l == part.labels[g]) continue;
+      bool dup = false;
+      for (int t = 0; t < ns; ++t) dup |= seen[t] == l;
+      if (!dup) seen[ns++] = l;
+    }
+    if (ns >= 2) part.cross.push_back((int32_t)g);
+  }
+  // grid marks within 2 N_O grid steps (inclusive, Euclidean) of any cross-point node
+  const int rad = 2 * n_overlap;
+  int32_t mlo[3], mdim[3];
+  for (int a = 0; a < 3; ++a) {
+    mlo[a] = B.lo[a] - rad;
+    mdim[a] = B.dims[a] + 2 * rad;
+  }
+  std::vector<uint8_t> mark((size_t)mdim[0] * mdim[1] * mdim[2], 0);
+  for (int32_t g : part.cross) {
+    const int32_t* q = &B.ijk[3 * (size_t)g];
+    for (int a = -rad; a <= rad; ++a)
+      for (int b = -rad; b <= rad; ++b)
+        for (int c = -rad; c <= rad; ++c) {
+          if (a * a + b * b + c * c > rad * rad) continue;
+          size_t o = ((size_t)(q[0] + a - mlo[0]) * mdim[1] + (q[1] + b - mlo[1])) * mdim[2] + (q[2] + c - mlo[2]);
+          mark[o] = 1;
+        }
+  }
+  auto near_cross = [&](int32_t g) {
+    const int32_t* q = &B.ijk[3 * (size_t)g];
+    return mark[((size_t)(q[0] - mlo[0]) * mdim[1] + (q[1] - mlo[1])) * mdim[2] + (q[2] - mlo[2])];
+  };
+
+  part.subs.resize(n_sub);
+  for (int64_t g = 0; g < na; ++g) part.subs[part.labels[g]].own.push_back((int32_t)g);
+  const int P = B.P(), P2 = P * P;
+  int failed = 0;
+#pragma omp parallel
+  {
+    std::vector<int32_t> dist(na, -1), tag(N, -1);
+    std::vector<int32_t> touched;
+#pragma omp for schedule(dynamic, 1)
+    for (int j = 0; j < n_sub; ++j) {
+      SubSets& S = part.subs[j];
+      touched.clear();
+      for (int32_t g : S.own) {
+        dist[g] = 0;
+        touched.push_back(g);
+      }
+      // BFS over the active 6-neighbour graph, N_O layers (Sec. 4.1)
+      std::vector<int32_t> front = S.own, next;
+      for (int layer = 1; layer <= n_overlap; ++layer) {
+        next.clear();
+        for (int32_t g : front)
+          for (int m = 0; m < 6; ++m) {
+            int32_t q = B.nbr[6 * (size_t)g + m];
+            if (q < na && dist[q] < 0) {
+              dist[q] = layer;
+              next.push_back(q);
+              touched.push_back(q);
+            }
+          }
+        front.swap(next);
+      }
+      for (int32_t g : touched) {
+        S.sigma.push_back(g);
+        if (dist[g] == n_overlap) S.last.push_back(g);
+      }
+      sort_unique(S.sigma);
+      sort_unique(S.last);
+      // tags: 1 = Sigma_j, 2 = Sigma_j^G, 3 = BC active, 4 = BC ghost layer
+      for (int32_t g : S.sigma) tag[g] = 1;
+      for (int32_t g : S.sigma)
+        for (int m = 0; m < 6; ++m) {
+          int32_t q = B.nbr[6 * (size_t)g + m];
+          if (q >= na) {
+            if (tag[q] != 2) { tag[q] = 2; S.ghost.push_back(q); }
+          } else if (tag[q] != 1 && tag[q] != 3) {
+            tag[q] = 3;
+            S.bc_a.push_back(q);
+          }
+        }
+      sort_unique(S.ghost);
+      auto add_stencil = [&](int32_t g) {
+        for (int s = 0; s < P2; ++s) {
+          int32_t st = B.pencil[(size_t)g * P2 + s];
+          for (int e = 0; e < P; ++e) {
+            int32_t q = st + e;
+            if (tag[q] != 1 && tag[q] != 3) { tag[q] = 3; S.bc_a.push_back(q); }
+          }
+        }
+      };
+      for (int32_t g : S.sigma) add_stencil(g);
+      for (int32_t g : S.ghost) add_stencil(g);
+      sort_unique(S.bc_a);
+      for (int32_t g : S.bc_a)
+        for (int m = 0; m < 6; ++m) {
+          int32_t q = B.nbr[6 * (size_t)g + m];
+          if (tag[q] < 0) { tag[q] = 4; S.bc_g.push_back(q); }
+        }
+      sort_unique(S.bc_g);
+      // nearest Lambda_j point of every BC node (Eq. locCP, exhaustive, ties: lowest tag)
+      auto nearest = [&](int32_t g) -> int32_t {
+        double x[3] = {(double)B.ijk[3 * (size_t)g] * B.h, (double)B.ijk[3 * (size_t)g + 1] * B.h,
+                       (double)B.ijk[3 * (size_t)g + 2] * B.h};
+        double best = 0;
+        int32_t bi = -1;
+        for (int32_t t : S.last) {
+          const double* y = &B.cp[3 * (size_t)t];
+          double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+          double dd = (d0 * d0 + d1 * d1) + d2 * d2;
+          if (bi < 0 || dd < best) { best = dd; bi = t; }
+        }
+        return bi;
+      };
+      S.bc_gen.reserve(S.bc_a.size() + S.bc_g.size());
+      for (int32_t g : S.bc_a) S.bc_gen.push_back(nearest(g));
+      for (int32_t g : S.bc_g) S.bc_gen.push_back(nearest(g));
+      for (int32_t g : S.bc_a) S.bc_nearx.push_back(near_cross(g));
+      for (int32_t g : S.bc_g) S.bc_nearx.push_back(near_cross(g));
+      if (!S.bc_a.empty() && S.last.empty()) {
+#pragma omp atomic
+        failed += 1;
+      }
+      // reset scratch
+      for (int32_t g : touched) dist[g] = -1;
+      for (int32_t g : S.sigma) tag[g] = -1;
+      for (int32_t g : S.ghost) tag[g] = -1;
+      for (int32_t g : S.bc_a) tag[g] = -1;
+      for (int32_t g : S.bc_g) tag[g] = -1;
+    }
+  }
+  if (failed) {
+    set_error("cpm_partition: a subdomain has boundary nodes but no last overlap layer");
+    return CPM_ERR_STENCIL;
+  }
+  return CPM_OK;
+}
+
+}  // namespace cpm

@@ -1,0 +1,119 @@
+"""C ABI without a GPU: the library loads, exports every declared entry point, and its
+host-side set-up (band, partition, node sets, local operators) matches the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1909_08734_gb300 as G
+from paper_1909_08734_gb300 import _capi
+from oracle import band as ob
+from oracle import geometry, interp, local, operator, partition
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "cpm.h")
+
+
+def _declared_functions():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", src, re.M)
+    return sorted(set(n for n in names if n.startswith(("cpm_", "oras_"))))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _capi.load()
+    names = _declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(_capi._SIGS), set(names) - set(_capi._SIGS)
+
+
+def test_status_strings():
+    assert G.status_string(0) == "CPM_OK"
+    assert G.status_string(10) == "CPM_ERR_STENCIL"
+
+
+def test_invalid_arguments_are_reported():
+    with pytest.raises(G.CpmError) as e:
+        G.cpm_build_band("sphere", 1.0, 0.0, -0.1, 3)
+    assert e.value.status == _capi.CPM_ERR_INVALID_ARG
+    with pytest.raises(G.CpmError) as e:
+        G.cpm_build_band("sphere", 1.0, 0.0, 0.1, 3, lambda_over_h=1.0)
+    assert e.value.status == _capi.CPM_ERR_STENCIL
+    band = G.cpm_build_band("sphere", 1.0, 0.0, 0.2, 3)
+    with pytest.raises(G.CpmError):
+        G.cpm_partition(band, 0, None, 2)
+    with pytest.raises(G.CpmError):
+        G.cpm_partition(band, 4, [1, 2, 0, 4], 2)
+    with pytest.raises(G.CpmError):
+        G.cpm_partition(band, 4, None, 2, align_passes=1)
+
+
+CASES = [("sphere", 1.0, 0.0, 0.1, 3, 8, 2, None),
+         ("sphere", 1.0, 0.0, 0.1, 2, 6, 3, None),
+         ("torus", 1.0, 0.4, 0.05, 3, 16, 2, [256, 1024, 300, 500, 999, 700, 260, 800,
+                                             400, 410, 420, 1000, 256, 257, 900, 333])]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-h{c[3]}-p{c[4]}-S{c[5]}")
+def pair(request):
+    kind, R, r, h, p, ns, no, w = request.param
+    band = G.cpm_build_band(kind, R, r, h, p)
+    part = G.cpm_partition(band, ns, w, no)
+    OB = ob.build_band(geometry.make_surface(kind, R, r), h, p)
+    E = interp.extension_matrix(OB)
+    lab = partition.rcb(OB.cp[:OB.n_active], ns, w)
+    return band, part, OB, E, lab, ns, no
+
+
+def test_band_bit_exact(pair):
+    band, part, OB, E, lab, ns, no = pair
+    inf = band.info()
+    assert inf["n_active"] == OB.n_active and inf["n_ghost"] == OB.n_ghost
+    assert np.array_equal(inf["ijk"], OB.ijk)
+    assert np.array_equal(inf["cp"], OB.cp)
+    assert np.array_equal(inf["nbr"], OB.nbr)
+    base, _ = interp.stencil_base(OB.cp, OB.h, OB.p)
+    assert np.array_equal(inf["base"], base)
+
+
+def test_partition_and_sets_bit_exact(pair):
+    band, part, OB, E, lab, ns, no = pair
+    assert np.array_equal(part.labels(), lab)
+    cross = partition.cross_point_nodes(OB, lab)
+    assert np.array_equal(part.cross_points(), cross)
+    marks = partition.CrossMarks(OB, cross, no)
+    for j in range(ns):
+        sub = partition.build_subdomain(OB, E, lab, j, no, robin=True)
+        for which, ref in [(G.CPM_SET_OWN, sub.own), (G.CPM_SET_SIGMA, sub.sigma),
+                           (G.CPM_SET_LAST, sub.last), (G.CPM_SET_GHOST, sub.ghost),
+                           (G.CPM_SET_BC_A, sub.bc_a), (G.CPM_SET_BC_G, sub.bc_g)]:
+            assert np.array_equal(part.set(j, which), ref), (j, which)
+        nodes = np.concatenate([sub.bc_a, sub.bc_g])
+        _, gen = partition.effective_boundary_cp(OB, sub, nodes)
+        assert np.array_equal(part.set(j, G.CPM_SET_BC_GEN), gen)
+        assert np.array_equal(part.set(j, G.CPM_SET_BC_NEARX).astype(bool), marks(nodes))
+
+
+@pytest.mark.parametrize("tr", ["ras", "oras", "oras_r3"])
+def test_local_operators_match_oracle(pair, tr):
+    band, part, OB, E, lab, ns, no = pair
+    c = 10.0
+    A = operator.cpm_matrix(OB, E, c)
+    cross = partition.cross_point_nodes(OB, lab)
+    marks = partition.CrossMarks(OB, cross, no)
+    for j in range(0, ns, max(1, ns // 4)):
+        sub = partition.build_subdomain(OB, E, lab, j, no, robin=(tr == "oras"))
+        if tr == "ras":
+            lp = local.ras_local(A, sub)
+        else:
+            lp = local.oras_local(OB, sub, c, 4.0, 40.0, marks, "R1" if tr == "oras" else "R3")
+        n, rr, cc, vv = G.cpm_local_coo(band, part, c, tr, 4.0, 40.0, j)
+        assert n == lp.n
+        D = np.zeros((n, n))
+        D[rr, cc] = vv
+        Do = lp.A.toarray()
+        # same sums of the same FP64 products, possibly in another order
+        assert np.abs(D - Do).max() <= 8 * np.finfo(float).eps * np.abs(Do).max()

@@ -1,0 +1,191 @@
+"""GPU parity through the C ABI against the CPU FP64 oracle (needs a GB300).
+
+Tolerances follow from the arithmetic:
+  operator apply  : each y_i is a sum of ~400 FP64 products, so
+                    |y_gpu - y_ref| <= 64 eps (|A| |x|)_i.
+  M^{-1} r, FP64  : both sides solve every A_j with a backward-stable LU, so they agree to
+                    ~cond(A_j) eps; cond(A_j) <= 1e5 here, bound 1e-10 relative.
+  M^{-1} r, FP32  : factor and solve in FP32, ~cond(A_j) 2^-24 relative -> 1e-3.
+  M^{-1} r, BF16  : factors stored in BF16 (8-bit mantissa) -> 5e-2.
+  GMRES, FP64     : converged to 1e-12, solution within 1e-10 relative of the oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import paper_1909_08734_gb300 as G  # noqa: E402
+from oracle import krylov, problems  # noqa: E402
+from workloads import random_vector  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(float).eps
+
+
+def _dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def sphere_small():
+    h, c = 0.1, 1.0
+    band = G.cpm_build_band("sphere", 1.0, 0.0, h, 3)
+    part = G.cpm_partition(band, 8, None, 2)
+    oras = problems.setup("sphere", 1.0, 0.0, h, 3, c, 8, 2, "oras", 4.0, 40.0)
+    ras = problems.setup("sphere", 1.0, 0.0, h, 3, c, 8, 2, "ras")
+    return band, part, oras, ras, c
+
+
+@pytest.fixture(scope="module")
+def torus_uneven():
+    h, c = 0.05, 10.0
+    w = np.array([256, 1024, 300, 500, 999, 700, 260, 800, 400, 410, 420, 1000, 256, 257, 900, 333])
+    band = G.cpm_build_band("torus", 1.0, 0.4, h, 3)
+    part = G.cpm_partition(band, 16, w, 2)
+    oras = problems.setup("torus", 1.0, 0.4, h, 3, c, 16, 2, "oras", 4.0, 40.0, leaf_weights=w)
+    return band, part, oras, c
+
+
+def test_operator_apply_parity(sphere_small):
+    band, part, oras, ras, c = sphere_small
+    pc = G.oras_setup(band, part, c, "ras", 0, 0, "fp64")
+    n = pc.n_active
+    X = np.stack([random_vector(n, s) for s in (1, 2, 3)])
+    x = _dev(X.ravel())
+    y = torch.empty_like(x)
+    G.cpm_op_apply(pc, x, y, nrhs=3)
+    Y = y.cpu().numpy().reshape(3, n)
+    absA = abs(oras.A)
+    for r in range(3):
+        ref = oras.A @ X[r]
+        bound = 64 * EPS * (absA @ np.abs(X[r])) + 1e-300
+        assert np.all(np.abs(Y[r] - ref) <= bound)
+
+
+def test_operator_maps_constants_to_c(torus_uneven):
+    band, part, oras, c = torus_uneven
+    pc = G.oras_setup(band, part, c, "ras", 0, 0, "fp64")
+    x = torch.ones(pc.n_active, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    G.cpm_op_apply(pc, x, y)
+    h = band.info()["h"]
+    assert torch.max(torch.abs(y - c)).item() <= 64 * EPS * (c + 12.0 / h ** 2)
+
+
+@pytest.mark.parametrize("method", ["ras", "oras"])
+def test_preconditioner_fp64_parity(sphere_small, method):
+    band, part, oras, ras, c = sphere_small
+    P = oras if method == "oras" else ras
+    pc = G.oras_setup(band, part, c, method, 4.0, 40.0, "fp64")
+    assert list(pc.local_sizes()) == [lp.n for lp in P.lps]
+    r = random_vector(pc.n_active, 7)
+    z = torch.empty(pc.n_active, dtype=torch.float64, device="cuda")
+    G.oras_apply(pc, _dev(r), z)
+    G.oras_check_status(pc)
+    ref = P.M.apply(r)
+    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= 1e-10, err
+
+
+def test_preconditioner_fp64_parity_uneven_torus(torus_uneven):
+    band, part, oras, c = torus_uneven
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, "fp64")
+    r = random_vector(pc.n_active, 8)
+    z = torch.empty(pc.n_active, dtype=torch.float64, device="cuda")
+    for _ in range(3):                       # repeated launches reuse the flags (epochs)
+        G.oras_apply(pc, _dev(r), z)
+    G.oras_check_status(pc)
+    ref = oras.M.apply(r)
+    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("bf16", 5e-2)])
+def test_preconditioner_low_precision(sphere_small, prec, tol):
+    band, part, oras, ras, c = sphere_small
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, prec)
+    r = random_vector(pc.n_active, 9)
+    z = torch.empty(pc.n_active, dtype=torch.float64, device="cuda")
+    G.oras_apply(pc, _dev(r), z)
+    G.oras_check_status(pc)
+    ref = oras.M.apply(r)
+    err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_gmres_fp64_matches_oracle(sphere_small, use_graph):
+    band, part, oras, ras, c = sphere_small
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, "fp64")
+    cp = band.info()["cp"][: pc.n_active]
+    f = (c + 12.0) * cp[:, 0] * cp[:, 1] * cp[:, 2]
+    u = torch.zeros(pc.n_active, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-12, use_graph=use_graph)[0]
+    ref = problems.solve(oras, f, 1e-12)
+    assert res["status"] == 0 and res["relres"] <= 1e-12
+    assert abs(res["iterations"] - ref.iterations) <= 1
+    err = np.linalg.norm(u.cpu().numpy() - ref.x) / np.linalg.norm(ref.x)
+    assert err <= 1e-10, err
+
+
+def test_gmres_kth_iterate_matches_oracle(sphere_small):
+    band, part, oras, ras, c = sphere_small
+    pc = G.oras_setup(band, part, c, "ras", 0, 0, "fp64")
+    f = random_vector(pc.n_active, 11)
+    for k in (1, 5, 12):
+        u = torch.zeros(pc.n_active, dtype=torch.float64, device="cuda")
+        res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-30, max_it=k, raise_on_failure=False)[0]
+        assert res["iterations"] == k and res["status"] == G._capi.CPM_ERR_NOT_CONVERGED
+        ref = krylov.fgmres(lambda x: ras.A @ x, ras.M.apply, f, 1e-30, 50, 1000, stop_after=k)
+        err = np.linalg.norm(u.cpu().numpy() - ref.x) / np.linalg.norm(ref.x)
+        assert err <= 1e-11, (k, err)
+
+
+def test_gmres_restarts(sphere_small):
+    band, part, oras, ras, c = sphere_small
+    pc = G.oras_setup(band, part, c, "ras", 0, 0, "fp64")
+    f = random_vector(pc.n_active, 12)
+    u = torch.zeros(pc.n_active, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-10, restart=5, max_it=500)[0]
+    ref = krylov.fgmres(lambda x: ras.A @ x, ras.M.apply, f, 1e-10, 5, 500)
+    assert res["status"] == 0 and abs(res["iterations"] - ref.iterations) <= 2
+    err = np.linalg.norm(u.cpu().numpy() - ref.x) / np.linalg.norm(ref.x)
+    assert err <= 1e-8, err
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_gmres_mixed_reaches_tolerance(torus_uneven, prec):
+    band, part, oras, c = torus_uneven
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, prec)
+    f = random_vector(pc.n_active, 13)
+    u = torch.zeros(pc.n_active, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-8)[0]
+    assert res["status"] == 0 and res["relres"] <= 1e-8
+    ref = problems.solve(oras, f, 1e-12)
+    err = np.linalg.norm(u.cpu().numpy() - ref.x) / np.linalg.norm(ref.x)
+    assert err <= 1e-6, err
+
+
+def test_zero_rhs_and_multi_rhs(sphere_small):
+    band, part, oras, ras, c = sphere_small
+    pc = G.oras_setup(band, part, c, "ras", 0, 0, "fp64")
+    n = pc.n_active
+    F = np.stack([np.zeros(n), random_vector(n, 14)])
+    u = torch.zeros(2 * n, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(F.ravel()), u, nrhs=2, tol=1e-10)
+    assert res[0]["status"] == 0 and res[0]["iterations"] == 0
+    assert torch.count_nonzero(u[:n]).item() == 0
+    assert res[1]["status"] == 0 and res[1]["relres"] <= 1e-10
+
+
+def test_one_subdomain_is_direct_solve():
+    band = G.cpm_build_band("sphere", 1.0, 0.0, 0.2, 3)
+    part = G.cpm_partition(band, 1, None, 2)
+    pc = G.oras_setup(band, part, 1.0, "oras", 4.0, 40.0, "fp64")
+    P = problems.setup("sphere", 1.0, 0.0, 0.2, 3, 1.0, 1, 2, "oras")
+    f = random_vector(pc.n_active, 15)
+    u = torch.zeros(pc.n_active, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-12)[0]
+    assert res["iterations"] == 1
+    import scipy.sparse.linalg as spla
+    ud = spla.spsolve(P.A.tocsc(), f)
+    assert np.linalg.norm(u.cpu().numpy() - ud) <= 1e-10 * np.linalg.norm(ud)
