@@ -153,6 +153,8 @@ typedef struct {
   int64_t device_bytes;       /* all device bytes held by the handle */
   double setup_ms_assemble;   /* device time of the assembly launch(es) */
   double setup_ms_factor;     /* device time of the batched LU launches */
+  int64_t kernel_launches;    /* library kernels launched by this handle so far (setup
+                                 excluded; graph replays count every kernel node) */
 } oras_info;
 cpm_status oras_info_get(const oras_precond* pc, oras_info* out);
 /* Local sizes n_j (host array of n_sub int64 written by the call). */

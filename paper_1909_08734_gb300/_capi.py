@@ -42,7 +42,8 @@ class oras_info(C.Structure):
                 ("precision", C.c_int), ("transmission", C.c_int), ("max_n", C.c_int64),
                 ("sum_n", C.c_int64), ("sum_n2", C.c_int64), ("sum_sigma", C.c_int64),
                 ("factor_bytes", C.c_int64), ("device_bytes", C.c_int64),
-                ("setup_ms_assemble", C.c_double), ("setup_ms_factor", C.c_double)]
+                ("setup_ms_assemble", C.c_double), ("setup_ms_factor", C.c_double),
+                ("kernel_launches", C.c_int64)]
 
 
 class cpm_gmres_opts(C.Structure):

@@ -64,6 +64,7 @@ struct oras_precond {
   std::vector<SubMeta> meta;
   int64_t sum_n = 0, sum_n2 = 0, sum_sigma = 0, rows_total = 0, tiles_total = 0;
   double ms_assemble = 0, ms_factor = 0;
+  int64_t launches = 0;       // kernels launched after setup (graph nodes included)
   std::vector<DevBuf> bufs;
   size_t device_bytes = 0, factor_bytes = 0;
   // device pointers
@@ -441,6 +442,7 @@ cpm_status launch_iteration(oras_precond* pc, cudaStream_t s) {
   CK(launch_trsv(pc->trsv, vk, zk, done, s));
   CK(launch_apply(pc->op, zk, pc->g_vext, nullptr, direct(g.w, 0), 1, 0, done, s));
   CK(launch_cgs2_and_givens(g, s));
+  pc->launches += KERNELS_PER_ITERATION;
   return CPM_OK;
 }
 
@@ -451,12 +453,16 @@ cpm_status solve_one(oras_precond* pc, const double* f, double* u, const cpm_gmr
   CK(launch_gmres_begin(g, f, o.tol, o.max_it, s));
   CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(g.r, 0), 1, 1, nullptr, s));
   CK(launch_gmres_residual_check(g, s));
+  pc->launches += KERNELS_BEGIN + KERNELS_APPLY + KERNELS_RESIDUAL_CHECK;
   for (;;) {
     CK(cudaMemcpyAsync(pc->g_istate_host, g.ist, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (pc->g_istate_host[3] != -1) break;     // converged or failed
     for (int it = 0; it < g.m; ++it) {
-      if (pc->iter_graph) CK(cudaGraphLaunch(pc->iter_graph, s));
+      if (pc->iter_graph) {
+        CK(cudaGraphLaunch(pc->iter_graph, s));
+        pc->launches += KERNELS_PER_ITERATION;
+      }
       else {
         cpm_status st = launch_iteration(pc, s);
         if (st != CPM_OK) return st;
@@ -465,6 +471,7 @@ cpm_status solve_one(oras_precond* pc, const double* f, double* u, const cpm_gmr
     CK(launch_gmres_restart_update(g, u, s));
     CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(g.r, 0), 1, 1, nullptr, s));
     CK(launch_gmres_residual_check(g, s));
+    pc->launches += KERNELS_RESTART_UPDATE + KERNELS_APPLY + KERNELS_RESIDUAL_CHECK;
   }
   CK(cudaMemcpy(pc->g_state_host, g.st + gmres_scalar_offset(g.m), 8 * sizeof(double),
                 cudaMemcpyDeviceToHost));
@@ -548,6 +555,7 @@ cpm_status oras_info_get(const oras_precond* pc, oras_info* o) {
   o->device_bytes = (int64_t)pc->device_bytes;
   o->setup_ms_assemble = pc->ms_assemble;
   o->setup_ms_factor = pc->ms_factor;
+  o->kernel_launches = pc->launches;
   return CPM_OK;
 }
 
@@ -569,6 +577,7 @@ cpm_status cpm_op_apply(const oras_precond* cpc, const double* x_dev, double* y_
   }
   cpm_status st = ensure_v_scratch(pc, nrhs);
   if (st != CPM_OK) return st;
+  pc->launches += KERNELS_APPLY;
   CK(launch_apply(pc->op, direct(const_cast<double*>(x_dev), pc->n_active), pc->v_scratch, nullptr,
                   direct(y_dev, pc->n_active), nrhs, 0, nullptr, (cudaStream_t)stream));
   return CPM_OK;
@@ -580,6 +589,7 @@ cpm_status oras_apply(const oras_precond* pc, const double* r_dev, double* z_dev
     cpm::set_error("oras_apply: bad argument");
     return CPM_ERR_INVALID_ARG;
   }
+  const_cast<oras_precond*>(pc)->launches += nrhs;
   for (int i = 0; i < nrhs; ++i)
     CK(launch_trsv(pc->trsv, direct(const_cast<double*>(r_dev) + (int64_t)i * pc->n_active, 0),
                    direct(z_dev + (int64_t)i * pc->n_active, 0), nullptr, (cudaStream_t)stream));

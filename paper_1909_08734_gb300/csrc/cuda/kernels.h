@@ -32,6 +32,15 @@ struct OperatorDev {
   double diag, invh2;
 };
 
+// kernels issued by each launcher (for the handle's launch counter)
+constexpr int KERNELS_APPLY = 2;
+constexpr int KERNELS_TRSV = 1;
+constexpr int KERNELS_CGS2_GIVENS = 8;
+constexpr int KERNELS_PER_ITERATION = KERNELS_TRSV + KERNELS_APPLY + KERNELS_CGS2_GIVENS;
+constexpr int KERNELS_BEGIN = 2;
+constexpr int KERNELS_RESTART_UPDATE = 2;
+constexpr int KERNELS_RESIDUAL_CHECK = 3;
+
 cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
                          IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s);
 
