@@ -81,6 +81,11 @@ typedef struct {
   const double* cp;       /* host, (N_A+N_G) x 3 closest points CP_S(x) */
   const int32_t* nbr;     /* host, N_A x 6 node indices of (-x,+x,-y,+y,-z,+z) neighbours */
   const int32_t* base;    /* host, (N_A+N_G) x 3 lowest interpolation-stencil node of CP(x) */
+  const int32_t* pencil;  /* host, (N_A+N_G) x (p+1)^2 active index of the first node of each
+                             z-pencil (a,b) of the stencil, a slowest; the pencil is p+1
+                             consecutive actives */
+  const double* weights;  /* host, (N_A+N_G) x 3 x (p+1) barycentric weights at CP(x): x axis,
+                             then y, then z */
 } cpm_band_info;
 
 /* Band construction (Sec. 2.1, tube-radius construction).

@@ -76,6 +76,8 @@ class Band:
             "cp": arr(inf.cp, 3 * n, np.float64).reshape(n, 3),
             "nbr": arr(inf.nbr, 6 * inf.n_active, np.int64).reshape(inf.n_active, 6),
             "base": arr(inf.base, 3 * n, np.int64).reshape(n, 3),
+            "pencil": arr(inf.pencil, n * (inf.p + 1) ** 2, np.int32).reshape(n, (inf.p + 1) ** 2),
+            "weights": arr(inf.weights, n * 3 * (inf.p + 1), np.float64).reshape(n, 3, inf.p + 1),
         }
 
 

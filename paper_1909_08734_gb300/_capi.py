@@ -34,7 +34,8 @@ class cpm_surface(C.Structure):
 class cpm_band_info(C.Structure):
     _fields_ = [("n_active", C.c_int64), ("n_ghost", C.c_int64), ("p", C.c_int), ("h", C.c_double),
                 ("lambda_", C.c_double), ("ijk", C.POINTER(C.c_int32)), ("cp", C.POINTER(C.c_double)),
-                ("nbr", C.POINTER(C.c_int32)), ("base", C.POINTER(C.c_int32))]
+                ("nbr", C.POINTER(C.c_int32)), ("base", C.POINTER(C.c_int32)),
+                ("pencil", C.POINTER(C.c_int32)), ("weights", C.POINTER(C.c_double))]
 
 
 class oras_info(C.Structure):

@@ -69,6 +69,8 @@ cpm_status cpm_band_info_get(const cpm_band* band, cpm_band_info* out) {
   out->cp = B.cp.data();
   out->nbr = B.nbr.data();
   out->base = B.base.data();
+  out->pencil = B.pencil.data();
+  out->weights = B.wts.data();
   return CPM_OK;
 }
 
