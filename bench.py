@@ -123,6 +123,25 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def run_kernel_only(args):
+    """Set up one preconditioner and launch only the batched solve (for profiler captures)."""
+    import torch
+    import paper_1909_08734_gb300 as G
+    from workloads import WORKLOADS, leaf_weights
+    wl = WORKLOADS[args.workload]
+    band = G.cpm_build_band(wl.surface, wl.R, wl.r, wl.h, wl.p)
+    part = G.cpm_partition(band, wl.n_sub, leaf_weights(wl.n_sub, wl.weight_seed), wl.n_overlap)
+    pc = G.oras_setup(band, part, wl.c, wl.method, wl.alpha, wl.alpha_x, args.precision)
+    r = torch.randn(pc.n_active, dtype=torch.float64, device="cuda")
+    z = torch.empty_like(r)
+    for _ in range(args.kernel_only):
+        G.oras_apply(pc, r, z)
+    torch.cuda.synchronize()
+    G.oras_check_status(pc)
+    print(json.dumps({"workload": wl.name, "precision": args.precision, "launches": args.kernel_only,
+                      **{k: v for k, v in pc.info().items() if k in ("factor_bytes", "sum_n2", "n_sub")}}))
+
+
 def run_native(args):
     import torch
     import paper_1909_08734_gb300 as G
@@ -375,10 +394,15 @@ def main():
     ap.add_argument("--workload", default="sphere_h0025")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--kernel-only", type=int, default=0,
+                    help="profiling aid: only N launches of the batched solve, no JSON bench line")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.kernel_only:
+        run_kernel_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_native(args)

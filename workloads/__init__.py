@@ -58,6 +58,9 @@ WORKLOADS = {
     "torus_h00125": Workload("torus_h00125", "torus", 1.0, 0.4, 0.0125, 3, 10.0, "torus_modes",
                              512, 2, "oras", 4.0, 40.0, "bf16", 1e-8,
                              weight_seed=3, rhs_seed=33),
+    # small case of the same kernels for profiler captures (factors ~1.5 GB, above L2)
+    "sphere_h005": Workload("sphere_h005", "sphere", 1.0, 0.0, 0.05, 3, 1.0, "xyz",
+                            16, 3, "oras", 4.0, 40.0, "fp32", 1e-8),
 }
 
 
