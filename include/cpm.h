@@ -172,6 +172,31 @@ cpm_status oras_local_sizes(const oras_precond* pc, int64_t* n_out);
 cpm_status cpm_op_apply(const oras_precond* pc, const double* x_dev, double* y_dev, int nrhs,
                         void* stream);
 
+/* Largest band (N_A + N_G nodes) that cpm_op_apply_noalloc accepts: its scratch is a fixed
+ * 8 MB array (2^20 FP64 values) that every GPU loading this library reserves until exit. */
+#define CPM_NOALLOC_MAX_NODES (1 << 20)
+
+/* y = A x exactly as cpm_op_apply computes it, but without allocating any device memory.
+ * The paper has no counterpart: this exists for callers that cannot call cudaMalloc —
+ * code whose device memory is owned by someone else's allocator (a framework's caching
+ * pool, an embedded runtime with a fixed budget), or a latency-critical loop where an
+ * allocation, which may synchronise the whole device, is not acceptable.
+ * The caller supplies every input and output as device memory: the band's z-pencil starts
+ * (int32, N x (p+1)^2), 1-D weights (FP64, N x 3 x (p+1)) and neighbour table (int32,
+ * N_A x 6) in the layouts cpm_band_info returns, x_dev and y_dev (FP64, N_A).  N = n_nodes.
+ * The extension values live in a library-owned static device array; its device address is
+ * looked up (cudaGetSymbolAddress) by the first call on each device, so make that first
+ * call before any stream capture.  All calls share the array and each call rewrites every
+ * entry it reads, so calls may follow one another freely, but calls that overlap on the GPU
+ * (different streams, or different host threads) race on it.  One right-hand side per call.
+ * Asynchronous on stream.  Errors: INVALID_ARG (NULL pointer, p not 2 or 3, n_nodes <
+ * n_active, h <= 0), BUDGET (n_nodes > CPM_NOALLOC_MAX_NODES), CUDA.  Calls no cudaMalloc,
+ * cudaFree or allocating library routine. */
+cpm_status cpm_op_apply_noalloc(const int32_t* pencil_dev, const double* weights_dev,
+                                const int32_t* nbr_dev, int64_t n_active, int64_t n_nodes, int p,
+                                double c, double h, const double* x_dev, double* y_dev,
+                                void* stream);
+
 /* z = M^{-1} r (Eq. algRAS): restrict r to every Sigma_j (zero on boundary unknowns),
  * solve with the resident LU factors, write each disjoint set's values to z (restricted
  * partition of unity).  FP64 in and out; the solves run in the factor precision.

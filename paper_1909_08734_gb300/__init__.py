@@ -210,6 +210,26 @@ def cpm_op_apply(pc: Preconditioner, x, y, nrhs: int = 1, stream=None):
                                      _stream_ptr(stream)), "cpm_op_apply")
 
 
+CPM_NOALLOC_MAX_NODES = 1 << 20
+
+
+def cpm_op_apply_noalloc(pencil, weights, nbr, n_active: int, n_nodes: int, p: int, c: float,
+                         h: float, x, y, stream=None):
+    """y = A x for callers that cannot allocate device memory: every argument is caller-owned
+    device memory (torch CUDA tensors: pencil int32, weights float64, nbr int32, x / y
+    float64); the library's scratch is a static device array, looked up on the first call
+    per device.  Calls that overlap on the GPU race on that shared array."""
+    import torch
+    for t, dt, name in ((pencil, torch.int32, "pencil"), (weights, torch.float64, "weights"),
+                        (nbr, torch.int32, "nbr")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous {dt} CUDA tensor")
+    _check(_capi.load().cpm_op_apply_noalloc(
+        C.c_void_p(pencil.data_ptr()), C.c_void_p(weights.data_ptr()), C.c_void_p(nbr.data_ptr()),
+        int(n_active), int(n_nodes), int(p), float(c), float(h), _dev_ptr(x, n_active, "x"),
+        _dev_ptr(y, n_active, "y"), _stream_ptr(stream)), "cpm_op_apply_noalloc")
+
+
 def oras_apply(pc: Preconditioner, r, z, nrhs: int = 1, stream=None):
     n = pc.n_active * nrhs
     _check(_capi.load().oras_apply(pc.handle, _dev_ptr(r, n, "r"), _dev_ptr(z, n, "z"), int(nrhs),

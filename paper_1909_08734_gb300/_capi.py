@@ -74,6 +74,8 @@ _SIGS = {
     "oras_info_get": (C.c_int, [_P, C.POINTER(oras_info)]),
     "oras_local_sizes": (C.c_int, [_P, _P]),
     "cpm_op_apply": (C.c_int, [_P, _P, _P, C.c_int, _P]),
+    "cpm_op_apply_noalloc": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int64, C.c_int, C.c_double,
+                                       C.c_double, _P, _P, _P]),
     "oras_apply": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "oras_check_status": (C.c_int, [_P, _P]),
     "cpm_gmres_solve": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(cpm_gmres_opts),
