@@ -183,8 +183,6 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   pc->n_sigma.resize(ns);
   int64_t tile_off = 0, row_off = 0, nnz = 0;
   int t_max = 0;
-  std::vector<int64_t> flag_off(ns);
-  int64_t flags_total = 0;
   for (int j = 0; j < ns; ++j) {
     const int64_t n = coo[j].n;
     const int T = (int)((n + TILE - 1) / TILE);
@@ -204,8 +202,6 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
     pc->sum_n += n;
     pc->sum_n2 += n * n;
     pc->sum_sigma += coo[j].n_sigma;
-    flag_off[j] = flags_total;
-    flags_total += 2 * T;
   }
   pc->t_max = t_max;
   pc->rows_total = row_off;
@@ -301,6 +297,13 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   const int use_tc = 0;
   for (int step = 0; step < t_max; ++step) CK(launch_lu_step(f, step, use_tc, s));
   CK(launch_lu_finish(f, d_unk, d_unk_off, d_own, pc->gather, pc->scatter, dinv, s));
+  void* inv;
+  {
+    cudaError_t e;
+    inv = pc->alloc(2 * wbytes * (size_t)row_off * TILE, &e);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc diagonal-block inverses");
+  }
+  CK(launch_diag_inverse(work, fp64, pc->d_meta, ns, t_max, inv, s));
   CK(cudaEventRecord(e2, s));
   CK(cudaStreamSynchronize(s));
   float ms1 = 0, ms2 = 0;
@@ -346,33 +349,26 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
     for (int j = 0; j < ns; ++j)
       if (t < pc->meta[j].T) items.push_back(make_int2(j, (pc->meta[j].T - 1 - t) | (1 << 30)));
   int2* d_items;
-  uint32_t *d_flags, *d_sync;
-  int64_t* d_flag_off;
+  uint32_t* d_sync;
+  uint64_t* d_ytag;
+  const int words = fp64 ? 2 : 1;             // tagged 64-bit words per published value
   ALLOC(d_items, int2, items.size());
-  ALLOC(d_flags, uint32_t, flags_total);
   ALLOC(d_sync, uint32_t, 4);
-  ALLOC(d_flag_off, int64_t, ns);
-  void* ybuf;
-  {
-    cudaError_t e;
-    ybuf = pc->alloc(wbytes * (size_t)row_off, &e);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc solve scratch");
-  }
+  ALLOC(d_ytag, uint64_t, (int64_t)words * row_off);
   CK(cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(d_flag_off, flag_off.data(), 8 * ns, cudaMemcpyHostToDevice));
-  CK(cudaMemset(d_flags, 0, 4 * flags_total));
+  CK(cudaMemset(d_ytag, 0, 8 * (size_t)words * row_off));
   CK(cudaMemset(d_sync, 0, 16));
+  pc->release(dinv);
+  pc->dinv = nullptr;
   TrsvDev& t = pc->trsv;
   t.tiles = pc->tiles;
-  t.dinv = dinv;
+  t.inv = inv;
   t.meta = pc->d_meta;
   t.gather = pc->gather;
   t.scatter = pc->scatter;
   t.items = d_items;
   t.n_items = (int)items.size();
-  t.y = ybuf;
-  t.flags = d_flags;
-  t.flag_off = d_flag_off;
+  t.ytag = d_ytag;
   t.sync = d_sync;
   t.status = pc->status;
   t.precision = precision;
@@ -416,7 +412,8 @@ cpm_status ensure_gmres(oras_precond* pc, int m) {
   const int64_t n = pc->n_active;
   g.n = n;
   g.m = m;
-  g.nblk = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+  // two blocks of 256 threads per SM for the Arnoldi kernels (rows split evenly)
+  g.nblk = (int)std::min<int64_t>((n + 255) / 256, 2 * (int64_t)sm_count(pc->device));
   if (g.nblk < 1) g.nblk = 1;
   ALLOC(g.V, double, (int64_t)(m + 1) * n);
   ALLOC(g.Z, double, (int64_t)m * n);
@@ -424,8 +421,8 @@ cpm_status ensure_gmres(oras_precond* pc, int m) {
   ALLOC(g.r, double, n);
   ALLOC(g.part, double, (int64_t)g.nblk * (m + 2));
   ALLOC(g.st, double, gmres_state_size(m));
-  ALLOC(g.ist, int, 8);
-  CK(cudaMemset(g.ist, 0, 8 * sizeof(int)));
+  ALLOC(g.ist, int, 16);
+  CK(cudaMemset(g.ist, 0, 16 * sizeof(int)));
   if (!pc->g_istate_host) CK(cudaMallocHost(&pc->g_istate_host, 8 * sizeof(int)));
   if (!pc->g_state_host) CK(cudaMallocHost(&pc->g_state_host, 8 * sizeof(double)));
   pc->g_m = m;

@@ -13,6 +13,7 @@ namespace cpmdev {
 
 __device__ __forceinline__ bool skip_iteration(const int* done) { return done && *done; }
 
+// 4 lanes per band node; lane a < P sums its x-slab: wx_a sum_b wy_b sum_c wz_c x[...]
 template <int P>
 __global__ void __launch_bounds__(256) ext_values_kernel(const int32_t* __restrict__ pencil,
                                                          const double* __restrict__ wts,
@@ -22,21 +23,29 @@ __global__ void __launch_bounds__(256) ext_values_kernel(const int32_t* __restri
   if (skip_iteration(done)) return;
   const double* xv = x.ptr(blockIdx.y);
   double* vv = v + (int64_t)blockIdx.y * n_nodes;
-  const int lane = threadIdx.x & 15;
-  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int a = threadIdx.x & 3;
+  const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   double part = 0.0;
-  if (k < n_nodes && lane < P * P) {
-    const int a = lane / P, b = lane % P;
+  if (k < n_nodes && a < P) {
     const double* w = wts + k * 3 * P;
-    const int32_t st = __ldg(pencil + k * (P * P) + lane);
-    double s = 0.0;
+    const int32_t* pk = pencil + k * (P * P) + a * P;
+    double wz[P];
 #pragma unroll
-    for (int c = 0; c < P; ++c) s += __ldg(w + 2 * P + c) * __ldg(xv + st + c);
-    part = (__ldg(w + a) * __ldg(w + P + b)) * s;
+    for (int c = 0; c < P; ++c) wz[c] = __ldg(w + 2 * P + c);
+    double t = 0.0;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      const int32_t st = __ldg(pk + b);
+      double s = 0.0;
+#pragma unroll
+      for (int c = 0; c < P; ++c) s += wz[c] * __ldg(xv + st + c);
+      t += __ldg(w + P + b) * s;
+    }
+    part = __ldg(w + a) * t;
   }
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, 16);
-  if (k < n_nodes && lane == 0) vv[k] = part;
+  part += __shfl_xor_sync(0xffffffffu, part, 1, 4);
+  part += __shfl_xor_sync(0xffffffffu, part, 2, 4);
+  if (k < n_nodes && a == 0) vv[k] = part;
 }
 
 // mode 0: y = A x;  mode 1: y = f - A x
@@ -63,7 +72,7 @@ __global__ void __launch_bounds__(256) nbr_sum_kernel(const int32_t* __restrict_
 cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
                          IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s) {
   const int64_t n = op.n_nodes;
-  dim3 g1((unsigned)((n * 16 + 255) / 256), nrhs);
+  dim3 g1((unsigned)((n * 4 + 255) / 256), nrhs);
   if (op.P == 4)
     ext_values_kernel<4><<<g1, 256, 0, s>>>(op.pencil, op.wts, x, v_scratch, n, op.n_active, done);
   else

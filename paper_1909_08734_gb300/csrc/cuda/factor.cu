@@ -281,6 +281,57 @@ cudaError_t launch_lu_finish(const FactorDev& f, const int32_t* unknowns, const 
   return cudaGetLastError();
 }
 
+// Inverses of the diagonal blocks of every tile row: Linv = L_II^{-1} (unit lower) and
+// Uinv = U_II^{-1} (upper), stored column-major in the compute precision C at
+// inv + ((row_off/64 + I) * 2 + {0: L, 1: U}) * 4096.  The triangular solves then apply a
+// diagonal block as one parallel matrix-vector product instead of a 64-step substitution.
+template <typename T, typename C>
+__global__ void __launch_bounds__(64) diag_inverse_kernel(const T* a, const SubMeta* __restrict__ meta,
+                                                          C* inv) {
+  const SubMeta m = meta[blockIdx.y];
+  const int I = blockIdx.x;
+  if (I >= m.T) return;
+  __shared__ C D[64][65];
+  const T* td = a + tile_base(m, I, I);
+  for (int e = threadIdx.x; e < 4096; e += 64) {
+    int i = e & 63, j = e >> 6;
+    D[i][j] = (C)td[Layout<T>::off(i, j)];
+  }
+  __syncthreads();
+  const int c = threadIdx.x;
+  C* li = inv + (((m.row_off >> 6) + I) * 2) * (int64_t)TILE_ELEMS;
+  C* ui = li + TILE_ELEMS;
+  C x[64];
+  // column c of L^{-1}: x_r = delta_rc - sum_{k<r} L_rk x_k (x_r = 0 for r < c)
+#pragma unroll
+  for (int r = 0; r < 64; ++r) {
+    C s = (r == c) ? (C)1 : (C)0;
+#pragma unroll
+    for (int k = 0; k < r; ++k) s -= D[r][k] * x[k];
+    x[r] = r < c ? (C)0 : s;
+  }
+#pragma unroll
+  for (int r = 0; r < 64; ++r) li[off_plain(r, c)] = x[r];
+  // column c of U^{-1}: x_r = (delta_rc - sum_{k>r} U_rk x_k) / U_rr (x_r = 0 for r > c)
+#pragma unroll
+  for (int r = 63; r >= 0; --r) {
+    C s = (r == c) ? (C)1 : (C)0;
+#pragma unroll
+    for (int k = r + 1; k < 64; ++k) s -= D[r][k] * x[k];
+    x[r] = r > c ? (C)0 : s / D[r][r];
+  }
+#pragma unroll
+  for (int r = 0; r < 64; ++r) ui[off_plain(r, c)] = x[r];
+}
+
+cudaError_t launch_diag_inverse(const void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
+                                void* inv, cudaStream_t s) {
+  dim3 g(t_max, n_sub);
+  if (fp64) diag_inverse_kernel<double, double><<<g, 64, 0, s>>>((const double*)a, meta, (double*)inv);
+  else diag_inverse_kernel<float, float><<<g, 64, 0, s>>>((const float*)a, meta, (float*)inv);
+  return cudaGetLastError();
+}
+
 __global__ void pack_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ out,
                                  int64_t n_tiles) {
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {

@@ -35,11 +35,11 @@ struct OperatorDev {
 // kernels issued by each launcher (for the handle's launch counter)
 constexpr int KERNELS_APPLY = 2;
 constexpr int KERNELS_TRSV = 1;
-constexpr int KERNELS_CGS2_GIVENS = 8;
+constexpr int KERNELS_CGS2_GIVENS = 4;
 constexpr int KERNELS_PER_ITERATION = KERNELS_TRSV + KERNELS_APPLY + KERNELS_CGS2_GIVENS;
-constexpr int KERNELS_BEGIN = 2;
+constexpr int KERNELS_BEGIN = 1;
 constexpr int KERNELS_RESTART_UPDATE = 2;
-constexpr int KERNELS_RESIDUAL_CHECK = 3;
+constexpr int KERNELS_RESIDUAL_CHECK = 2;
 
 cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
                          IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s);
@@ -63,19 +63,20 @@ cudaError_t launch_lu_finish(const FactorDev& f, const int32_t* unknowns, const 
                              const int32_t* own_flag, int32_t* gather, int32_t* scatter,
                              void* dinv, cudaStream_t s);
 cudaError_t launch_pack_bf16(const float* a, __nv_bfloat16* out, int64_t n_tiles, cudaStream_t s);
+cudaError_t launch_diag_inverse(const void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
+                                void* inv, cudaStream_t s);
 
 // ---- batched local solves ----
 struct TrsvDev {
   const void* tiles;       // factor tiles (double / float swizzled / bf16)
-  const void* dinv;        // 1/U_ii per padded row (double for FP64, float otherwise)
+  const void* inv;         // per tile row: L_II^{-1}, U_II^{-1} (compute precision, column-major)
   const SubMeta* meta;
   const int32_t* gather;   // per padded row: global active index of the permuted local row or -1
   const int32_t* scatter;  // per padded row: global index if the unknown is owned, else -1
   const int2* items;       // (subdomain, tile row | direction bit 30)
   int n_items;
-  void* y;                 // per padded row scratch (compute precision)
-  uint32_t* flags;         // 2 per tile row: forward, backward
-  const int64_t* flag_off; // per subdomain offset into flags
+  uint64_t* ytag;          // per padded row: published value(s) tagged with the launch epoch
+                           // (1 word for FP32: tag<<32 | bits; 2 words for FP64: hi, lo)
   uint32_t* sync;          // [0] item counter, [1] finished CTAs, [2] epoch, [3] abort
   int* status;
   int precision;           // 0 fp64, 1 fp32, 2 bf16

@@ -1,9 +1,16 @@
 // Device-resident right-preconditioned flexible GMRES(m) with CGS2 (Sec. 2.2: the (O)RAS
-// preconditioner inside GMRES).  All Arnoldi arithmetic is FP64.  Reductions are two-stage
-// (per-block partial sums in a fixed order, then a fixed-order sum over blocks), so results
-// do not depend on scheduling.  The step index k, the cycle-done flag and the status live
-// in device memory, so one captured CUDA graph of an iteration replays for every k; every
-// kernel of an iteration returns at once when the cycle is already done.
+// preconditioner inside GMRES).  All Arnoldi arithmetic is FP64.
+//
+// Reductions are deterministic: every block writes its partial sums, and the last block to
+// finish (ticket counter) adds the partials in block order.  The step index k, the
+// cycle-done flag and the status live in device memory, so one captured CUDA graph of an
+// iteration replays for every k; every kernel of an iteration returns at once when the
+// cycle is already done.  One Arnoldi step after z_k = M^{-1} v_k and w = A z_k is four
+// kernels:
+//   dots    : h1 = V_k^T w                                   (first Gram-Schmidt pass)
+//   update1 : w -= V_k h1 ;  h2 = V_k^T w                    (second pass)
+//   update2 : w -= V_k h2 ;  ||w||, Hessenberg column, Givens rotation, stopping test
+//   scale   : v_{k+1} = w / ||w|| ;  k += 1
 #include <math.h>
 
 #include "../../../include/cpm.h"
@@ -14,9 +21,11 @@ namespace cpmdev {
 
 constexpr int KT = 256;                 // threads per block of the vector kernels
 constexpr int KW = KT / 32;
+constexpr int ILP = 8;                  // basis vectors processed together
 
 // int state
-enum { I_K = 0, I_TOTAL = 1, I_DONE = 2, I_STATUS = 3, I_KDONE = 4, I_MAXIT = 5 };
+enum { I_K = 0, I_TOTAL = 1, I_DONE = 2, I_STATUS = 3, I_KDONE = 4, I_MAXIT = 5,
+       I_TICKET = 8 };                  // tickets 8..11, one per reducing kernel
 constexpr int RUNNING = -1;
 
 // double state layout for restart length m
@@ -37,103 +46,151 @@ __device__ __forceinline__ bool cycle_done(const GmresDev& g) {
   return *(volatile const int*)&g.ist[I_DONE] != 0;
 }
 
-// part[b * (m+2) + i] = sum over block b's rows of V_i[row] * w[row], i = 0..k
-__global__ void __launch_bounds__(KT) mdot_kernel(GmresDev g) {
-  if (cycle_done(g)) return;
-  __shared__ double wp[KW][130];
-  const int k = g.ist[I_K];
+__device__ __forceinline__ void block_rows(const GmresDev& g, int64_t* r0, int64_t* r1) {
   const int64_t chunk = (g.n + g.nblk - 1) / g.nblk;
-  const int64_t r0 = blockIdx.x * chunk, r1 = min(g.n, r0 + chunk);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i <= k; ++i) {
-    const double* Vi = g.V + (int64_t)i * g.n;
-    double s = 0.0;
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) s += Vi[row] * g.w[row];
-    s = warp_sum(s);
-    if (lane == 0) wp[warp][i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i <= k; i += KT) {
-    double s = 0.0;
-    for (int w = 0; w < KW; ++w) s += wp[w][i];
-    g.part[(int64_t)blockIdx.x * (g.m + 2) + i] = s;
-  }
+  *r0 = blockIdx.x * chunk;
+  *r1 = min(g.n, *r0 + chunk);
 }
 
-// out[i] = sum_b part[b][i] for i = 0..cnt-1 (cnt = k+1, or 1 for a norm)
-__global__ void reduce_kernel(GmresDev g, int out_off, int norm_only) {
-  if (cycle_done(g)) return;
-  const int cnt = norm_only ? 1 : g.ist[I_K] + 1;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < g.nblk; ++b) s += g.part[(int64_t)b * (g.m + 2) + i];
-    g.st[out_off + i] = s;
-  }
-}
-
-// w -= V h (i = 0..k); with dots: part[b][i] = sum V_i[row] * w_new[row];
-// without: part[b][0] = sum w_new[row]^2
-__global__ void __launch_bounds__(KT) cgs_update_kernel(GmresDev g, int h_off, int dots) {
-  if (cycle_done(g)) return;
-  __shared__ double hs[130];
-  __shared__ double wp[KW][130];
-  const int k = g.ist[I_K];
-  for (int i = threadIdx.x; i <= k; i += KT) hs[i] = g.st[h_off + i];
-  __syncthreads();
-  const int64_t chunk = (g.n + g.nblk - 1) / g.nblk;
-  const int64_t r0 = blockIdx.x * chunk, r1 = min(g.n, r0 + chunk);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-    double w = g.w[row];
-    for (int i = 0; i <= k; ++i) w -= g.V[(int64_t)i * g.n + row] * hs[i];
-    g.w[row] = w;
-  }
-  __syncthreads();
-  const int cnt = dots ? k + 1 : 1;
-  for (int i = 0; i < cnt; ++i) {
-    double s = 0.0;
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-      const double w = g.w[row];
-      s += dots ? g.V[(int64_t)i * g.n + row] * w : w * w;
-    }
-    s = warp_sum(s);
-    if (lane == 0) wp[warp][i] = s;
-  }
-  __syncthreads();
+// Block partial sums s[i] (i < cnt, held in shared memory wp[KW][...]) -> part[b][i].
+// Then the last block adds all blocks' partials in block order into out[i].  Returns true
+// in the last block (after out[] is written and visible to that block).
+__device__ bool finish_reduction(const GmresDev& g, double (*wp)[130], int cnt, int ticket,
+                                 double* out) {
+  __shared__ bool last;
+  __shared__ double gsum[4][130];
   for (int i = threadIdx.x; i < cnt; i += KT) {
     double s = 0.0;
     for (int w = 0; w < KW; ++w) s += wp[w][i];
     g.part[(int64_t)blockIdx.x * (g.m + 2) + i] = s;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&g.ist[ticket], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  // 4 groups of 64 threads: group q adds blocks q, q+4, ...; then the groups in order
+  const int q = threadIdx.x >> 6, i = threadIdx.x & 63;
+  for (int i0 = 0; i0 < cnt; i0 += 64) {
+    if (i0 + i < cnt) {
+      double s = 0.0;
+      for (int b = q; b < g.nblk; b += 4) s += __ldcg(g.part + (int64_t)b * (g.m + 2) + i0 + i);
+      gsum[q][i0 + i] = s;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < cnt; t += KT) out[t] = ((gsum[0][t] + gsum[1][t]) + gsum[2][t]) + gsum[3][t];
+  if (threadIdx.x == 0) g.ist[ticket] = 0;
+  __syncthreads();
+  return true;
 }
 
-// Hessenberg column, Givens rotations, residual estimate, stopping decision.
-__global__ void givens_kernel(GmresDev g) {
-  if (cycle_done(g) || threadIdx.x != 0) return;
+// h1 = V_k^T w
+__global__ void __launch_bounds__(KT) dots_kernel(GmresDev g) {
+  if (cycle_done(g)) return;
+  __shared__ double wp[KW][130];
+  const int k = g.ist[I_K];
+  int64_t r0, r1;
+  block_rows(g, &r0, &r1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 <= k; i0 += ILP) {
+    double acc[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) acc[u] = 0.0;
+    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+      const double w = g.w[row];
+#pragma unroll
+      for (int u = 0; u < ILP; ++u)
+        if (i0 + u <= k) acc[u] += g.V[(int64_t)(i0 + u) * g.n + row] * w;
+    }
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      const double s = warp_sum(acc[u]);
+      if (lane == 0 && i0 + u <= k) wp[warp][i0 + u] = s;
+    }
+  }
+  __syncthreads();
   const SL L{g.m};
+  finish_reduction(g, wp, k + 1, I_TICKET + 0, g.st + L.h1());
+}
+
+// w -= V_k h (h at st[h_off]); then either dots with the new w (into h2) or ||w||^2 with
+// the Hessenberg / Givens update in the last block.
+__global__ void __launch_bounds__(KT) update_kernel(GmresDev g, int h_off, int dots) {
+  if (cycle_done(g)) return;
+  __shared__ double hs[130];
+  __shared__ double wp[KW][130];
+  __shared__ double total[130];
+  const int k = g.ist[I_K];
+  for (int i = threadIdx.x; i <= k; i += KT) hs[i] = g.st[h_off + i];
+  __syncthreads();
+  int64_t r0, r1;
+  block_rows(g, &r0, &r1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+    double a[ILP];
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) a[u] = 0.0;
+    for (int i0 = 0; i0 <= k; i0 += ILP)
+#pragma unroll
+      for (int u = 0; u < ILP; ++u)
+        if (i0 + u <= k) a[u] += g.V[(int64_t)(i0 + u) * g.n + row] * hs[i0 + u];
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) s += a[u];
+    g.w[row] -= s;
+  }
+  const SL L{g.m};
+  if (dots) {
+    for (int i0 = 0; i0 <= k; i0 += ILP) {
+      double acc[ILP];
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) acc[u] = 0.0;
+      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+        const double w = g.w[row];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u)
+          if (i0 + u <= k) acc[u] += g.V[(int64_t)(i0 + u) * g.n + row] * w;
+      }
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) {
+        const double s = warp_sum(acc[u]);
+        if (lane == 0 && i0 + u <= k) wp[warp][i0 + u] = s;
+      }
+    }
+    __syncthreads();
+    finish_reduction(g, wp, k + 1, I_TICKET + 1, g.st + L.h2());
+    return;
+  }
+  double s = 0.0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) s += g.w[row] * g.w[row];
+  s = warp_sum(s);
+  if (lane == 0) wp[warp][0] = s;
+  __syncthreads();
+  if (!finish_reduction(g, wp, 1, I_TICKET + 2, total)) return;
+  if (threadIdx.x != 0) return;
+  // Hessenberg column k, previous rotations, new rotation, residual estimate
   double* st = g.st;
   int* ist = g.ist;
-  const int k = ist[I_K];
-  double ss = 0.0;
-  for (int b = 0; b < g.nblk; ++b) ss += g.part[(int64_t)b * (g.m + 2)];
-  const double hn = sqrt(ss);
+  const double hn = sqrt(total[0]);
   for (int i = 0; i <= k; ++i) st[L.H(i, k)] = st[L.h1() + i] + st[L.h2() + i];
   st[L.H(k + 1, k)] = hn;
   for (int i = 0; i < k; ++i) {
-    const double c = st[L.cs() + i], s = st[L.sn() + i];
+    const double c = st[L.cs() + i], sv = st[L.sn() + i];
     const double a = st[L.H(i, k)], b = st[L.H(i + 1, k)];
-    st[L.H(i, k)] = c * a + s * b;
-    st[L.H(i + 1, k)] = -s * a + c * b;
+    st[L.H(i, k)] = c * a + sv * b;
+    st[L.H(i + 1, k)] = -sv * a + c * b;
   }
   const double a = st[L.H(k, k)], b = st[L.H(k + 1, k)];
   const double rho = sqrt(a * a + b * b);
-  const double c = a / rho, s = b / rho;
+  const double c = a / rho, sv = b / rho;
   st[L.cs() + k] = c;
-  st[L.sn() + k] = s;
+  st[L.sn() + k] = sv;
   st[L.H(k, k)] = rho;
   st[L.H(k + 1, k)] = 0.0;
   const double gk = st[L.g() + k];
-  st[L.g() + k + 1] = -s * gk;
+  st[L.g() + k + 1] = -sv * gk;
   st[L.g() + k] = c * gk;
   st[L.sc() + S_HN] = hn;
   ist[I_TOTAL] += 1;
@@ -148,55 +205,53 @@ __global__ void givens_kernel(GmresDev g) {
   if (stop) ist[I_DONE] = 1;
 }
 
-// V[k+1] = w / ||w||
-__global__ void __launch_bounds__(KT) scale_next_kernel(GmresDev g) {
+// v_{k+1} = w / ||w||, then the last block advances k
+__global__ void __launch_bounds__(KT) scale_kernel(GmresDev g) {
   if (cycle_done(g)) return;
+  __shared__ bool last;
   const SL L{g.m};
   const int k = g.ist[I_K];
   const double inv = 1.0 / g.st[L.sc() + S_HN];
   double* dst = g.V + (int64_t)(k + 1) * g.n;
   for (int64_t row = (int64_t)blockIdx.x * KT + threadIdx.x; row < g.n; row += (int64_t)gridDim.x * KT)
     dst[row] = g.w[row] * inv;
-}
-
-__global__ void advance_kernel(GmresDev g) {
-  if (cycle_done(g)) return;
-  g.ist[I_K] += 1;
-}
-
-// ---- cycle start / restart ------------------------------------------------------------
-// part[b][0] = sum over block b of x[row]^2
-__global__ void __launch_bounds__(KT) norm_partial_kernel(GmresDev g, const double* x) {
-  __shared__ double wp[KW];
-  const int64_t chunk = (g.n + g.nblk - 1) / g.nblk;
-  const int64_t r0 = blockIdx.x * chunk, r1 = min(g.n, r0 + chunk);
-  double s = 0.0;
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) s += x[row] * x[row];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < KW; ++w) t += wp[w];
-    g.part[(int64_t)blockIdx.x * (g.m + 2)] = t;
+    last = atomicAdd(&g.ist[I_TICKET + 3], 1) == (int)gridDim.x - 1;
+    if (last) {
+      g.ist[I_TICKET + 3] = 0;
+      g.ist[I_K] = k + 1;
+    }
   }
 }
 
-__global__ void begin_kernel(GmresDev g, double tol, int max_it, int which) {
+// ---- cycle start / restart ------------------------------------------------------------
+// ||x||^2 over all blocks; the last block applies the begin (which = 0: ||f||) or the
+// convergence test on beta = ||r|| (which = 1).
+__global__ void __launch_bounds__(KT) norm_begin_kernel(GmresDev g, const double* x, double tol,
+                                                        int max_it, int which) {
+  __shared__ double wp[KW][130];
+  __shared__ double total[130];
+  int64_t r0, r1;
+  block_rows(g, &r0, &r1);
+  double s = 0.0;
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) s += x[row] * x[row];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5][0] = s;
+  __syncthreads();
+  if (!finish_reduction(g, wp, 1, I_TICKET + 3, total)) return;
   if (threadIdx.x != 0) return;
   const SL L{g.m};
-  double ss = 0.0;
-  for (int b = 0; b < g.nblk; ++b) ss += g.part[(int64_t)b * (g.m + 2)];
+  const double nrm = sqrt(total[0]);
   if (which == 0) {               // ||f||
-    g.st[L.sc() + S_NF] = sqrt(ss);
+    g.st[L.sc() + S_NF] = nrm;
     g.st[L.sc() + S_TOL] = tol;
     g.ist[I_MAXIT] = max_it;
     g.ist[I_TOTAL] = 0;
     g.ist[I_STATUS] = RUNNING;
     return;
   }
-  // which == 1: beta = ||r|| (cycle start or restart check)
-  const double beta = sqrt(ss);
+  const double beta = nrm;
   const double nf = g.st[L.sc() + S_NF];
   g.st[L.sc() + S_BETA] = beta;
   g.st[L.sc() + S_RELRES] = nf > 0.0 ? beta / nf : 0.0;
@@ -227,16 +282,21 @@ __global__ void __launch_bounds__(KT) start_basis_kernel(GmresDev g) {
     g.V[row] = g.r[row] * inv;
 }
 
-// y = H[:kd,:kd]^{-1} g[:kd] (back substitution), then u += Z y
+// y = H[:kd,:kd]^{-1} g[:kd] by one warp (back substitution), then u += Z y
 __global__ void ysolve_kernel(GmresDev g) {
-  if (threadIdx.x != 0) return;
   const SL L{g.m};
+  __shared__ double ys[129];
   const int kd = g.ist[I_KDONE];
+  for (int i = threadIdx.x; i < kd; i += 32) ys[i] = g.st[L.g() + i];
+  __syncwarp();
   for (int i = kd - 1; i >= 0; --i) {
-    double s = g.st[L.g() + i];
-    for (int q = i + 1; q < kd; ++q) s -= g.st[L.H(i, q)] * g.st[L.y() + q];
-    g.st[L.y() + i] = s / g.st[L.H(i, i)];
+    double s = 0.0;
+    for (int q = i + 1 + threadIdx.x; q < kd; q += 32) s += g.st[L.H(i, q)] * ys[q];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) ys[i] = (ys[i] - s) / g.st[L.H(i, i)];
+    __syncwarp();
   }
+  for (int i = threadIdx.x; i < kd; i += 32) g.st[L.y() + i] = ys[i];
 }
 
 __global__ void __launch_bounds__(KT) xupdate_kernel(GmresDev g, double* u) {
@@ -246,9 +306,17 @@ __global__ void __launch_bounds__(KT) xupdate_kernel(GmresDev g, double* u) {
   for (int i = threadIdx.x; i < kd; i += KT) ys[i] = g.st[L.y() + i];
   __syncthreads();
   for (int64_t row = (int64_t)blockIdx.x * KT + threadIdx.x; row < g.n; row += (int64_t)gridDim.x * KT) {
-    double s = u[row];
-    for (int i = 0; i < kd; ++i) s += g.Z[(int64_t)i * g.n + row] * ys[i];
-    u[row] = s;
+    double a[ILP];
+#pragma unroll
+    for (int u2 = 0; u2 < ILP; ++u2) a[u2] = 0.0;
+    for (int i0 = 0; i0 < kd; i0 += ILP)
+#pragma unroll
+      for (int u2 = 0; u2 < ILP; ++u2)
+        if (i0 + u2 < kd) a[u2] += g.Z[(int64_t)(i0 + u2) * g.n + row] * ys[i0 + u2];
+    double s = 0.0;
+#pragma unroll
+    for (int u2 = 0; u2 < ILP; ++u2) s += a[u2];
+    u[row] += s;
   }
 }
 
@@ -262,22 +330,16 @@ static unsigned vec_blocks(int64_t n) {
 
 cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, double tol, int max_it,
                                cudaStream_t s) {
-  norm_partial_kernel<<<g.nblk, KT, 0, s>>>(g, f);
-  begin_kernel<<<1, 32, 0, s>>>(g, tol, max_it, 0);
+  norm_begin_kernel<<<g.nblk, KT, 0, s>>>(g, f, tol, max_it, 0);
   return cudaGetLastError();
 }
 
-// one Arnoldi step after z_k = M^{-1} v_k and w = A z_k
 cudaError_t launch_cgs2_and_givens(const GmresDev& g, cudaStream_t s) {
   const SL L{g.m};
-  mdot_kernel<<<g.nblk, KT, 0, s>>>(g);
-  reduce_kernel<<<1, 128, 0, s>>>(g, L.h1(), 0);
-  cgs_update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h1(), 1);
-  reduce_kernel<<<1, 128, 0, s>>>(g, L.h2(), 0);
-  cgs_update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h2(), 0);
-  givens_kernel<<<1, 32, 0, s>>>(g);
-  scale_next_kernel<<<vec_blocks(g.n), KT, 0, s>>>(g);
-  advance_kernel<<<1, 1, 0, s>>>(g);
+  dots_kernel<<<g.nblk, KT, 0, s>>>(g);
+  update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h1(), 1);
+  update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h2(), 0);
+  scale_kernel<<<vec_blocks(g.n), KT, 0, s>>>(g);
   return cudaGetLastError();
 }
 
@@ -289,8 +351,7 @@ cudaError_t launch_gmres_restart_update(const GmresDev& g, double* u, cudaStream
 
 // after r = f - A u: beta, convergence decision, and V[0] = r / beta for the next cycle
 cudaError_t launch_gmres_residual_check(const GmresDev& g, cudaStream_t s) {
-  norm_partial_kernel<<<g.nblk, KT, 0, s>>>(g, g.r);
-  begin_kernel<<<1, 32, 0, s>>>(g, 0.0, 0, 1);
+  norm_begin_kernel<<<g.nblk, KT, 0, s>>>(g, g.r, 0.0, 0, 1);
   start_basis_kernel<<<vec_blocks(g.n), KT, 0, s>>>(g);
   return cudaGetLastError();
 }
