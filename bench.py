@@ -163,12 +163,16 @@ def run_native(args):
     cp = band.info()["cp"]
     pcs = {}
     setup_s = {}
+    schedules = {}
     for prec in ["fp32", "bf16", "fp64"] if not args.no_fp64 else ["fp32", "bf16"]:
         torch.cuda.synchronize()
         t = time.time()
         pcs[prec] = G.oras_setup(band, part, wl.c, wl.method, wl.alpha, wl.alpha_x, prec)
         torch.cuda.synchronize()
         setup_s[prec] = time.time() - t
+        t = time.time()
+        schedules[prec] = G.oras_autotune(pcs[prec])
+        setup_s[prec + "_autotune"] = time.time() - t
     pc = pcs["fp32"]
     n = pc.n_active
     f_host = rhs(wl, cp[:n])
@@ -254,20 +258,33 @@ def run_native(args):
     info = pc.info()
     r = torch.randn(n, dtype=torch.float64, device=dev)
     z = torch.empty_like(r)
-    for _ in range(3):
-        G.oras_apply(pc, r, z, stream=stream)
-    nl = 20
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(nl):
-        G.oras_apply(pc, r, z, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    G.oras_check_status(pc)
-    apply_ms = e0.elapsed_time(e1) / nl
+
+    def apply_time(p, nl=20):
+        for _ in range(3):
+            G.oras_apply(p, r, z, stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nl):
+            G.oras_apply(p, r, z, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        G.oras_check_status(p)
+        return e0.elapsed_time(e1) / nl
+
+    apply_ms = apply_time(pc)
     alg_bytes = 4 * info["sum_n2"] + 8 * info["sum_sigma"] + 8 * n
     peak, peak_kind = _peaks()
+    ms16 = apply_time(pcs["bf16"])
+    b16 = 2 * info["sum_n2"] + 8 * info["sum_sigma"] + 8 * n
+    extra["bf16"]["solve_kernel"] = {"launch_ms": round(ms16, 4), "achieved_gbs": round(b16 / ms16 / 1e6, 1),
+                                     "frac": round(b16 / ms16 / 1e6 / peak, 4)}
+    if "fp64" in pcs:
+        ms64 = apply_time(pcs["fp64"], 5)
+        b64 = 8 * info["sum_n2"] + 8 * info["sum_sigma"] + 8 * n
+        extra["fp64"]["solve_kernel"] = {
+            "launch_ms": round(ms64, 4), "achieved_gbs": round(b64 / ms64 / 1e6, 1),
+            "fp64_tflops": round(2 * info["sum_n2"] / ms64 / 1e9, 3), "bound": "fp64 alu"}
     achieved = alg_bytes / (apply_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": _profiled_traffic(),
@@ -324,6 +341,7 @@ def run_native(args):
         "setup_s": {"host_band_partition": round(host_setup_s, 3),
                     **{k: round(v, 3) for k, v in setup_s.items()},
                     "fp32_factor_ms": round(info["setup_ms_factor"], 2)},
+        "solve_schedule": schedules,
         "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
         "cpu_baseline": cpu_baseline, **extra,
     }

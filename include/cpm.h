@@ -53,8 +53,10 @@ enum {
   CPM_ORAS = 1,     /* Robin, every local unknown gets a 7-point row (reading R1)           */
   CPM_ORAS_R3 = 2   /* Robin, boundary unknowns get (c+6/h^2) w - (6/h^2) T w (reading R3)  */
 };
-/* precision of the local factors and local solves */
-enum { CPM_FP64 = 0, CPM_FP32 = 1, CPM_BF16 = 2 };
+/* precision of the local factors and local solves; CPM_SETUP_SIMT_LU may be or-ed into the
+ * precision argument of oras_setup to run the LU trailing updates on the CUDA cores instead
+ * of the tensor cores (a reference path for validating the tensor-core update) */
+enum { CPM_FP64 = 0, CPM_FP32 = 1, CPM_BF16 = 2, CPM_SETUP_SIMT_LU = 0x100 };
 /* node-set selectors for cpm_partition_set */
 enum { CPM_SET_OWN = 0, CPM_SET_SIGMA = 1, CPM_SET_LAST = 2, CPM_SET_GHOST = 3,
        CPM_SET_BC_A = 4, CPM_SET_BC_G = 5, CPM_SET_BC_GEN = 6, CPM_SET_BC_NEARX = 7 };
@@ -136,9 +138,11 @@ cpm_status cpm_local_coo(const cpm_band* band, const cpm_part* part, double c,
 
 /* Preconditioner setup (Sec. 5 local operators; "local operators" phase of Sec. 6.6):
  * uploads the band to the device, assembles every local matrix as a dense tile-major
- * matrix on the GPU, factors all of them with partial pivoting in batched launches
- * (precision CPM_FP64 / CPM_FP32 / CPM_BF16: BF16 inputs with FP32 accumulation, factors
- * stored in BF16) and keeps the factors resident.  Synchronises the stream.
+ * matrix on the GPU, factors all of them with partial pivoting in batched launches and
+ * keeps the factors resident.  CPM_FP64: FP64 throughout.  CPM_FP32: FP32 factors, trailing
+ * updates on the tensor cores with split-tf32 operands (FP32 accuracy).  CPM_BF16: trailing
+ * updates with bf16 operands and FP32 accumulation, factors stored in BF16 for the solves.
+ * Synchronises the stream.
  * Errors: INVALID_ARG, STENCIL, SINGULAR (zero pivot), OOM, CUDA. */
 cpm_status oras_setup(const cpm_band* band, const cpm_part* part, double c,
                       int transmission, double alpha, double alpha_x, int precision,
@@ -160,8 +164,30 @@ typedef struct {
   double setup_ms_factor;     /* device time of the batched LU launches */
   int64_t kernel_launches;    /* library kernels launched by this handle so far (setup
                                  excluded; graph replays count every kernel node) */
+  int solve_ctas_per_sm;      /* current schedule of the batched solve (see oras_tune) */
+  int solve_kseg;
+  int solve_prefetch;
+  int solve_stagger;
 } oras_info;
 cpm_status oras_info_get(const oras_precond* pc, oras_info* out);
+/* Schedule knobs of the batched local solve (oras_apply and the solves inside
+ * cpm_gmres_solve).  They change speed only, never results beyond rounding order:
+ *   CPM_TUNE_SOLVE_CTAS_PER_SM  persistent CTAs per SM (1 .. shared-memory limit)
+ *   CPM_TUNE_SOLVE_KSEG         off-diagonal 64x64 tiles per work item; longer tile rows
+ *                               are split into partial items (1 .. 1023; 1023 = no split)
+ *   CPM_TUNE_SOLVE_PREFETCH     1: a CTA holds its next work item and streams it early
+ *   CPM_TUNE_SOLVE_STAGGER      1: both sweeps in one queue, odd subdomains offset by half
+ *                               a sweep (overlaps sweep starts and tails across subdomains)
+ * Not thread-safe with concurrent calls on the same handle; invalidates the handle's
+ * captured iteration graph (recaptured on the next solve).  Errors: INVALID_ARG, OOM, CUDA. */
+enum { CPM_TUNE_SOLVE_CTAS_PER_SM = 0, CPM_TUNE_SOLVE_KSEG = 1, CPM_TUNE_SOLVE_PREFETCH = 2,
+       CPM_TUNE_SOLVE_STAGGER = 3 };
+cpm_status oras_tune(oras_precond* pc, int knob, int value);
+/* Project autotuner: times the batched solve on this handle's factors for a small grid of
+ * (CTAs per SM, split length, prefetch, stagger) candidates with CUDA events on `stream` and keeps
+ * the fastest.  Synchronises the stream.  The chosen values are in oras_info. */
+cpm_status oras_autotune(oras_precond* pc, void* stream);
+
 /* Local sizes n_j (host array of n_sub int64 written by the call). */
 cpm_status oras_local_sizes(const oras_precond* pc, int64_t* n_out);
 

@@ -196,10 +196,12 @@ def cpm_local_coo(band: Band, part: Partition, c: float, transmission: str, alph
 
 def oras_setup(band: Band, part: Partition, c: float, transmission: str = "oras",
                alpha: float = 4.0, alpha_x: float = 40.0, precision: str = "fp64",
-               stream=None) -> Preconditioner:
+               stream=None, simt_lu: bool = False) -> Preconditioner:
+    """simt_lu=True runs the LU trailing updates on the CUDA cores (validation reference)."""
     h_out = C.c_void_p()
+    prec = PRECISIONS[precision] | (_capi.CPM_SETUP_SIMT_LU if simt_lu else 0)
     _check(_capi.load().oras_setup(band.handle, part.handle, float(c), TRANSMISSIONS[transmission],
-                                   float(alpha), float(alpha_x), PRECISIONS[precision],
+                                   float(alpha), float(alpha_x), prec,
                                    _stream_ptr(stream), C.byref(h_out)), "oras_setup")
     return Preconditioner(h_out, band, part)
 
@@ -234,6 +236,23 @@ def oras_apply(pc: Preconditioner, r, z, nrhs: int = 1, stream=None):
     n = pc.n_active * nrhs
     _check(_capi.load().oras_apply(pc.handle, _dev_ptr(r, n, "r"), _dev_ptr(z, n, "z"), int(nrhs),
                                    _stream_ptr(stream)), "oras_apply")
+
+
+TUNE_KNOBS = {"ctas_per_sm": _capi.CPM_TUNE_SOLVE_CTAS_PER_SM, "kseg": _capi.CPM_TUNE_SOLVE_KSEG,
+              "prefetch": _capi.CPM_TUNE_SOLVE_PREFETCH, "stagger": _capi.CPM_TUNE_SOLVE_STAGGER}
+
+
+def oras_tune(pc: Preconditioner, **knobs):
+    """Set schedule knobs of the batched solve: ctas_per_sm=, kseg=, prefetch=, stagger=."""
+    for k, v in knobs.items():
+        _check(_capi.load().oras_tune(pc.handle, TUNE_KNOBS[k], int(v)), "oras_tune")
+
+
+def oras_autotune(pc: Preconditioner, stream=None) -> dict:
+    """Time the candidate schedules of the batched solve and keep the fastest."""
+    _check(_capi.load().oras_autotune(pc.handle, _stream_ptr(stream)), "oras_autotune")
+    inf = pc.info()
+    return {k: inf["solve_" + k] for k in ("ctas_per_sm", "kseg", "prefetch", "stagger")}
 
 
 def oras_check_status(pc: Preconditioner, stream=None):

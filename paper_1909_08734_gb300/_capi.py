@@ -21,8 +21,10 @@ CPM_ERR_BUDGET = 9
 CPM_ERR_STENCIL = 10
 # enums
 CPM_SPHERE, CPM_TORUS = 0, 1
+CPM_TUNE_SOLVE_CTAS_PER_SM, CPM_TUNE_SOLVE_KSEG, CPM_TUNE_SOLVE_PREFETCH, CPM_TUNE_SOLVE_STAGGER = 0, 1, 2, 3
 CPM_RAS, CPM_ORAS, CPM_ORAS_R3 = 0, 1, 2
 CPM_FP64, CPM_FP32, CPM_BF16 = 0, 1, 2
+CPM_SETUP_SIMT_LU = 0x100
 (CPM_SET_OWN, CPM_SET_SIGMA, CPM_SET_LAST, CPM_SET_GHOST, CPM_SET_BC_A, CPM_SET_BC_G,
  CPM_SET_BC_GEN, CPM_SET_BC_NEARX) = range(8)
 
@@ -44,7 +46,8 @@ class oras_info(C.Structure):
                 ("sum_n", C.c_int64), ("sum_n2", C.c_int64), ("sum_sigma", C.c_int64),
                 ("factor_bytes", C.c_int64), ("device_bytes", C.c_int64),
                 ("setup_ms_assemble", C.c_double), ("setup_ms_factor", C.c_double),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("solve_ctas_per_sm", C.c_int),
+                ("solve_kseg", C.c_int), ("solve_prefetch", C.c_int), ("solve_stagger", C.c_int)]
 
 
 class cpm_gmres_opts(C.Structure):
@@ -78,6 +81,8 @@ _SIGS = {
                                        C.c_double, _P, _P, _P]),
     "oras_apply": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "oras_check_status": (C.c_int, [_P, _P]),
+    "oras_tune": (C.c_int, [_P, C.c_int, C.c_int]),
+    "oras_autotune": (C.c_int, [_P, _P]),
     "cpm_gmres_solve": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(cpm_gmres_opts),
                                   C.POINTER(cpm_gmres_result), _P]),
     "oras_destroy": (None, [_P]),

@@ -21,8 +21,8 @@ LIB = os.path.join(HERE, "libcpm_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 HOST_SRC = ["host/band.cpp", "host/partition.cpp", "host/local_coo.cpp", "capi_host.cpp"]
-CUDA_SRC = ["cuda/apply.cu", "cuda/factor.cu", "cuda/trsv.cu", "cuda/krylov.cu", "capi_device.cu",
-            "noalloc.cu"]
+CUDA_SRC = ["cuda/apply.cu", "cuda/factor.cu", "cuda/lu_tc.cu", "cuda/trsv.cu", "cuda/krylov.cu",
+            "capi_device.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

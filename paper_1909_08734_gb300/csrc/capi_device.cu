@@ -65,6 +65,7 @@ struct oras_precond {
   int64_t sum_n = 0, sum_n2 = 0, sum_sigma = 0, rows_total = 0, tiles_total = 0;
   double ms_assemble = 0, ms_factor = 0;
   int64_t launches = 0;       // kernels launched after setup (graph nodes included)
+  int solve_ctas = 0;         // current CTAs per SM of the batched solve
   std::vector<DevBuf> bufs;
   size_t device_bytes = 0, factor_bytes = 0;
   // device pointers
@@ -144,8 +145,47 @@ int sm_count(int dev) {
   return n > 0 ? n : 1;
 }
 
+// Work-item queue and partial-sum slots of the batched solve for a split length kseg,
+// and its grid.  Drops the captured iteration graph (it holds the old schedule).
+cpm_status set_schedule(oras_precond* pc, int ctas_per_sm, int kseg, int prefetch, int stagger) {
+  TrsvDev& t = pc->trsv;
+  if (kseg != t.kseg || stagger != t.stagger || !t.items) {
+    std::vector<int2> items;
+    std::vector<int> Ts(pc->n_sub);
+    for (int j = 0; j < pc->n_sub; ++j) Ts[j] = pc->meta[j].T;
+    int maxseg = 1;
+    trsv_build_items(Ts.data(), pc->n_sub, kseg, stagger, items, &maxseg);
+    if (t.items) pc->release(const_cast<int2*>(t.items));
+    if (t.ptag) pc->release(t.ptag);
+    t.items = nullptr;
+    t.ptag = nullptr;
+    const int words = pc->precision == CPM_FP64 ? 2 : 1;
+    const int64_t nslot = (int64_t)words * (pc->rows_total / TILE) * maxseg * TILE;
+    int2* d_items;
+    uint64_t* d_ptag;
+    ALLOC(d_items, int2, items.size());
+    ALLOC(d_ptag, uint64_t, nslot);
+    CK(cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemset(d_ptag, 0, 8 * (size_t)nslot));
+    t.items = d_items;
+    t.n_items = (int)items.size();
+    t.ptag = d_ptag;
+    t.kseg = kseg;
+    t.stagger = stagger;
+    t.maxseg = maxseg;
+  }
+  t.prefetch = prefetch;
+  t.grid = sm_count(pc->device) * ctas_per_sm;
+  pc->solve_ctas = ctas_per_sm;
+  if (pc->iter_graph) {
+    cudaGraphExecDestroy(pc->iter_graph);
+    pc->iter_graph = nullptr;
+  }
+  return CPM_OK;
+}
+
 cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition& P, double c,
-                      int transmission, double alpha, double alpha_x, int precision,
+                      int transmission, double alpha, double alpha_x, int precision, bool simt_lu,
                       cudaStream_t s) {
   const int ns = P.n_sub;
   pc->band = &B;
@@ -294,7 +334,9 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   CK(launch_scatter(work, fp64, d_off, d_val, nnz, s));
   CK(cudaEventRecord(e1, s));
   FactorDev f{work, pc->d_meta, ipiv, pc->status, ns, t_max, fp64 ? 1 : 0};
-  const int use_tc = 0;
+  // FP32: split-tf32 tensor-core update (FP32 accuracy); BF16: bf16 inputs, FP32 accumulate
+  const int use_tc = (precision == CPM_FP64 || simt_lu) ? 0 : (precision == CPM_BF16 ? 2 : 1);
+  if (use_tc) CK(lu_tc_prepare());
   for (int step = 0; step < t_max; ++step) CK(launch_lu_step(f, step, use_tc, s));
   CK(launch_lu_finish(f, d_unk, d_unk_off, d_own, pc->gather, pc->scatter, dinv, s));
   void* inv;
@@ -341,21 +383,11 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   }
 
   // ---- persistent triangular-solve schedule ----
-  std::vector<int2> items;
-  for (int t = 0; t < t_max; ++t)
-    for (int j = 0; j < ns; ++j)
-      if (t < pc->meta[j].T) items.push_back(make_int2(j, t));
-  for (int t = 0; t < t_max; ++t)
-    for (int j = 0; j < ns; ++j)
-      if (t < pc->meta[j].T) items.push_back(make_int2(j, (pc->meta[j].T - 1 - t) | (1 << 30)));
-  int2* d_items;
   uint32_t* d_sync;
   uint64_t* d_ytag;
   const int words = fp64 ? 2 : 1;             // tagged 64-bit words per published value
-  ALLOC(d_items, int2, items.size());
   ALLOC(d_sync, uint32_t, 4);
   ALLOC(d_ytag, uint64_t, (int64_t)words * row_off);
-  CK(cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
   CK(cudaMemset(d_ytag, 0, 8 * (size_t)words * row_off));
   CK(cudaMemset(d_sync, 0, 16));
   pc->release(dinv);
@@ -366,14 +398,13 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   t.meta = pc->d_meta;
   t.gather = pc->gather;
   t.scatter = pc->scatter;
-  t.items = d_items;
-  t.n_items = (int)items.size();
   t.ytag = d_ytag;
   t.sync = d_sync;
   t.status = pc->status;
   t.precision = precision;
-  t.grid = sm_count(pc->device) * trsv_ctas_per_sm(precision);
   CK(trsv_prepare(precision));
+  st = set_schedule(pc, trsv_ctas_per_sm(precision), 1023, 0, 0);
+  if (st != CPM_OK) return st;
 
   // ---- operator ----
   OperatorDev& op = pc->op;
@@ -412,8 +443,8 @@ cpm_status ensure_gmres(oras_precond* pc, int m) {
   const int64_t n = pc->n_active;
   g.n = n;
   g.m = m;
-  // two blocks of 256 threads per SM for the Arnoldi kernels (rows split evenly)
-  g.nblk = (int)std::min<int64_t>((n + 255) / 256, 2 * (int64_t)sm_count(pc->device));
+  // one block of 256 threads per SM for the Arnoldi kernels (rows split evenly)
+  g.nblk = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(pc->device));
   if (g.nblk < 1) g.nblk = 1;
   ALLOC(g.V, double, (int64_t)(m + 1) * n);
   ALLOC(g.Z, double, (int64_t)m * n);
@@ -510,6 +541,8 @@ cpm_status oras_setup(const cpm_band* band, const cpm_part* part, double c, int 
     return CPM_ERR_INVALID_ARG;
   }
   *out = nullptr;
+  const bool simt_lu = (precision & CPM_SETUP_SIMT_LU) != 0;
+  precision &= ~CPM_SETUP_SIMT_LU;
   if (!(c > 0.0) || (precision != CPM_FP64 && precision != CPM_FP32 && precision != CPM_BF16) ||
       (transmission != CPM_RAS && transmission != CPM_ORAS && transmission != CPM_ORAS_R3) ||
       (transmission != CPM_RAS && !(alpha >= 0.0 && alpha_x >= 0.0))) {
@@ -520,7 +553,7 @@ cpm_status oras_setup(const cpm_band* band, const cpm_part* part, double c, int 
   try {
     pc = new oras_precond();
     cpm_status st = setup_impl(pc, band->b, part->p, c, transmission, alpha, alpha_x, precision,
-                               (cudaStream_t)stream);
+                               simt_lu, (cudaStream_t)stream);
     if (st != CPM_OK) {
       delete pc;
       return st;
@@ -553,6 +586,10 @@ cpm_status oras_info_get(const oras_precond* pc, oras_info* o) {
   o->setup_ms_assemble = pc->ms_assemble;
   o->setup_ms_factor = pc->ms_factor;
   o->kernel_launches = pc->launches;
+  o->solve_ctas_per_sm = pc->solve_ctas;
+  o->solve_kseg = pc->trsv.kseg;
+  o->solve_prefetch = pc->trsv.prefetch;
+  o->solve_stagger = pc->trsv.stagger;
   return CPM_OK;
 }
 
@@ -591,6 +628,69 @@ cpm_status oras_apply(const oras_precond* pc, const double* r_dev, double* z_dev
     CK(launch_trsv(pc->trsv, direct(const_cast<double*>(r_dev) + (int64_t)i * pc->n_active, 0),
                    direct(z_dev + (int64_t)i * pc->n_active, 0), nullptr, (cudaStream_t)stream));
   return CPM_OK;
+}
+
+cpm_status oras_tune(oras_precond* pc, int knob, int value) {
+  if (!pc) {
+    cpm::set_error("oras_tune: NULL handle");
+    return CPM_ERR_INVALID_ARG;
+  }
+  int ctas = pc->solve_ctas, kseg = pc->trsv.kseg, pf = pc->trsv.prefetch, sg = pc->trsv.stagger;
+  const int max_ctas = trsv_ctas_per_sm(pc->precision);
+  if (knob == CPM_TUNE_SOLVE_CTAS_PER_SM && value >= 1 && value <= max_ctas) ctas = value;
+  else if (knob == CPM_TUNE_SOLVE_KSEG && value >= 1 && value <= 1023) kseg = value;
+  else if (knob == CPM_TUNE_SOLVE_PREFETCH && (value == 0 || value == 1)) pf = value;
+  else if (knob == CPM_TUNE_SOLVE_STAGGER && (value == 0 || value == 1)) sg = value;
+  else {
+    cpm::set_error("oras_tune: unknown knob or value out of range (CTAs per SM 1.." +
+                   std::to_string(max_ctas) + ", kseg 1..1023, prefetch 0/1, stagger 0/1)");
+    return CPM_ERR_INVALID_ARG;
+  }
+  return set_schedule(pc, ctas, kseg, pf, sg);
+}
+
+cpm_status oras_autotune(oras_precond* pc, void* stream) {
+  if (!pc) {
+    cpm::set_error("oras_autotune: NULL handle");
+    return CPM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  double *r = nullptr, *z = nullptr;
+  CK(cudaMalloc(&r, 8 * pc->n_active));
+  CK(cudaMalloc(&z, 8 * pc->n_active));
+  CK(cudaMemsetAsync(r, 0, 8 * pc->n_active, s));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int max_ctas = trsv_ctas_per_sm(pc->precision);
+  const int ksegs[] = {8, 16, 32, 1023};
+  float best = 1e30f;
+  int bc = max_ctas, bk = 1023, bp = 0, bs = 0;
+  cpm_status st = CPM_OK;
+  for (int c = 1; c <= max_ctas && st == CPM_OK; ++c)
+    for (int k : ksegs)
+      for (int cand = 0; cand < 4 && st == CPM_OK; ++cand) {
+        const int pf = cand & 1, sg = cand >> 1;
+        st = set_schedule(pc, c, k, pf, sg);
+        if (st != CPM_OK) break;
+        for (int w = 0; w < 2; ++w) launch_trsv(pc->trsv, direct(r, 0), direct(z, 0), nullptr, s);
+        cudaEventRecord(e0, s);
+        for (int w = 0; w < 3; ++w) launch_trsv(pc->trsv, direct(r, 0), direct(z, 0), nullptr, s);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { st = cuda_fail(e, "oras_autotune"); break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bc = c; bk = k; bp = pf; bs = sg; }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(r);
+  cudaFree(z);
+  if (st != CPM_OK) return st;
+  st = set_schedule(pc, bc, bk, bp, bs);
+  if (st != CPM_OK) return st;
+  return oras_check_status(pc, stream);
 }
 
 cpm_status oras_check_status(const oras_precond* pc, void* stream) {

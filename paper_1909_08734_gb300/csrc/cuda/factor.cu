@@ -231,8 +231,13 @@ cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_
     lu_swap_kernel<float><<<dim3(f.t_max, f.n_sub), 64, 0, s>>>(a, f.meta, f.ipiv, step);
     if (W > 0) {
       lu_trsm_kernel<float><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step);
-      size_t sm = 2 * 64 * 65 * sizeof(float);
-      lu_update_simt_kernel<float><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max);
+      if (use_tc) {
+        cudaError_t e = launch_lu_update_tc(f, step, use_tc == 2, s);
+        if (e != cudaSuccess) return e;
+      } else {
+        size_t sm = 2 * 64 * 65 * sizeof(float);
+        lu_update_simt_kernel<float><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max);
+      }
     }
   }
   return cudaGetLastError();

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace cpmdev {
@@ -58,7 +60,10 @@ cudaError_t launch_scatter(void* a, int fp64, const int64_t* off, const double* 
                            cudaStream_t s);
 cudaError_t launch_pad_identity(void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
                                 cudaStream_t s);
+// use_tc: 0 SIMT update, 1 tensor cores with split-tf32 operands, 2 tensor cores with bf16
 cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_t s);
+cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s);
+cudaError_t lu_tc_prepare();
 cudaError_t launch_lu_finish(const FactorDev& f, const int32_t* unknowns, const int64_t* unk_off,
                              const int32_t* own_flag, int32_t* gather, int32_t* scatter,
                              void* dinv, cudaStream_t s);
@@ -73,10 +78,15 @@ struct TrsvDev {
   const SubMeta* meta;
   const int32_t* gather;   // per padded row: global active index of the permuted local row or -1
   const int32_t* scatter;  // per padded row: global index if the unknown is owned, else -1
-  const int2* items;       // (subdomain, tile row | direction bit 30)
+  const int2* items;       // (subdomain, tile row | segment << 20 | direction << 30)
   int n_items;
   uint64_t* ytag;          // per padded row: published value(s) tagged with the launch epoch
                            // (1 word for FP32: tag<<32 | bits; 2 words for FP64: hi, lo)
+  uint64_t* ptag;          // tagged partial sums: per tile row, maxseg segments x 64 rows
+  int kseg;                // off-diagonal tiles per work item (long rows are split)
+  int maxseg;
+  int prefetch;            // 1: a CTA holds its next item and streams it early
+  int stagger;             // 1: one queue for both sweeps with staggered subdomains
   uint32_t* sync;          // [0] item counter, [1] finished CTAs, [2] epoch, [3] abort
   int* status;
   int precision;           // 0 fp64, 1 fp32, 2 bf16
@@ -86,6 +96,11 @@ cudaError_t launch_trsv(const TrsvDev& t, IndirectVec r_in, IndirectVec z_out, c
                         cudaStream_t s);
 int trsv_ctas_per_sm(int precision);
 cudaError_t trsv_prepare(int precision);
+// Queue of work items for the batched solve: forward items, then backward items, each
+// sorted by the chain position they wait for (partial segments of a row before its
+// diagonal item).  T[j] = tiles per dimension of subdomain j.
+void trsv_build_items(const int* T, int n_sub, int kseg, int stagger, std::vector<int2>& items,
+                      int* maxseg);
 
 // ---- Krylov kernels ----
 struct GmresDev {

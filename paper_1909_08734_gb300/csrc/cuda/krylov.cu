@@ -74,9 +74,18 @@ __device__ bool finish_reduction(const GmresDev& g, double (*wp)[130], int cnt, 
   const int q = threadIdx.x >> 6, i = threadIdx.x & 63;
   for (int i0 = 0; i0 < cnt; i0 += 64) {
     if (i0 + i < cnt) {
-      double s = 0.0;
-      for (int b = q; b < g.nblk; b += 4) s += __ldcg(g.part + (int64_t)b * (g.m + 2) + i0 + i);
-      gsum[q][i0 + i] = s;
+      const double* p = g.part + i0 + i;
+      const int64_t ld = g.m + 2;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four loads in flight
+      int b = q;
+      for (; b + 12 < g.nblk; b += 16) {
+        s0 += __ldcg(p + (int64_t)b * ld);
+        s1 += __ldcg(p + (int64_t)(b + 4) * ld);
+        s2 += __ldcg(p + (int64_t)(b + 8) * ld);
+        s3 += __ldcg(p + (int64_t)(b + 12) * ld);
+      }
+      for (; b < g.nblk; b += 4) s0 += __ldcg(p + (int64_t)b * ld);
+      gsum[q][i0 + i] = (s0 + s1) + (s2 + s3);
     }
   }
   __syncthreads();

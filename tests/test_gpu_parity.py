@@ -189,3 +189,46 @@ def test_one_subdomain_is_direct_solve():
     import scipy.sparse.linalg as spla
     ud = spla.spsolve(P.A.tocsc(), f)
     assert np.linalg.norm(u.cpu().numpy() - ud) <= 1e-10 * np.linalg.norm(ud)
+
+
+def test_solve_schedules_agree(torus_uneven):
+    # every schedule of the batched solve computes the same M^{-1} r up to rounding order
+    band, part, oras, c = torus_uneven
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, "fp32")
+    r = _dev(random_vector(pc.n_active, 16))
+    z0 = torch.empty_like(r)
+    G.oras_apply(pc, r, z0)
+    for knobs in ({"kseg": 1}, {"kseg": 3, "prefetch": 1}, {"ctas_per_sm": 1, "kseg": 16},
+                  {"stagger": 1, "kseg": 5}, {"stagger": 1, "prefetch": 0, "kseg": 1023},
+                  {"kseg": 1023, "prefetch": 0, "ctas_per_sm": 2}):
+        G.oras_tune(pc, **knobs)
+        z = torch.empty_like(r)
+        for _ in range(2):
+            G.oras_apply(pc, r, z)
+        G.oras_check_status(pc)
+        assert (torch.linalg.norm(z - z0) / torch.linalg.norm(z0)).item() <= 1e-5, knobs
+    best = G.oras_autotune(pc)
+    assert 1 <= best["ctas_per_sm"] and 1 <= best["kseg"] <= 1023
+    u = torch.zeros_like(r)
+    res = G.cpm_gmres_solve(pc, r, u, tol=1e-8)[0]
+    assert res["status"] == 0
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16", 3e-2)])
+def test_tensor_core_lu_matches_cuda_core_lu(torus_uneven, prec, tol):
+    # the tcgen05 trailing update (split-tf32 for FP32, bf16 inputs for BF16) factors the
+    # same matrices as the CUDA-core update: M^{-1} r agrees to the factor precision
+    band, part, oras, c = torus_uneven
+    r = _dev(random_vector(oras.band.n_active, 17))
+    out = []
+    for simt in (False, True):
+        pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, prec, simt_lu=simt)
+        z = torch.empty_like(r)
+        G.oras_apply(pc, r, z)
+        G.oras_check_status(pc)
+        out.append(z)
+    err = (torch.linalg.norm(out[0] - out[1]) / torch.linalg.norm(out[1])).item()
+    assert err <= tol, err
+    ref = oras.M.apply(r.cpu().numpy())
+    err_ref = np.linalg.norm(out[0].cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err_ref <= (1e-3 if prec == "fp32" else 5e-2), err_ref
