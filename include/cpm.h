@@ -46,7 +46,7 @@ typedef enum {
 } cpm_status;
 
 /* surface kinds */
-enum { CPM_SPHERE = 0, CPM_TORUS = 1 };
+enum { CPM_SPHERE = 0, CPM_TORUS = 1, CPM_TRIMESH = 2 };
 /* transmission conditions (oras_setup) */
 enum {
   CPM_RAS = 0,      /* Dirichlet: A_j = R_j A R_j^T on Sigma_j (Eq. simpleRAS)              */
@@ -61,12 +61,21 @@ enum { CPM_FP64 = 0, CPM_FP32 = 1, CPM_BF16 = 2, CPM_SETUP_SIMT_LU = 0x100 };
 enum { CPM_SET_OWN = 0, CPM_SET_SIGMA = 1, CPM_SET_LAST = 2, CPM_SET_GHOST = 3,
        CPM_SET_BC_A = 4, CPM_SET_BC_G = 5, CPM_SET_BC_GEN = 6, CPM_SET_BC_NEARX = 7 };
 
-/* Surface with an analytic closest point (Sec. 2.1): sphere of radius R at the origin, or
- * the torus about the z axis with major radius R and minor radius r. */
+/* Surface (Sec. 2.1).  CPM_SPHERE: radius R at the origin.  CPM_TORUS: about the z axis,
+ * major radius R, minor radius r.  CPM_TRIMESH: a closed triangulated surface given by
+ * verts (host, n_verts x 3 doubles) and tris (host, n_tris x 3 vertex indices, any winding);
+ * CP_S(x) is the exact closest point over all triangles (ties: lowest triangle index) and
+ * the surface normal at a closest point is the unit face normal of its triangle.  The mesh
+ * arrays are copied by cpm_build_band; R and r are ignored for meshes, the mesh fields for
+ * analytic surfaces. */
 typedef struct {
   int kind;
   double R;
   double r;
+  const double* verts;
+  int64_t n_verts;
+  const int32_t* tris;
+  int64_t n_tris;
 } cpm_surface;
 
 typedef struct cpm_band cpm_band;
@@ -88,6 +97,7 @@ typedef struct {
                              consecutive actives */
   const double* weights;  /* host, (N_A+N_G) x 3 x (p+1) barycentric weights at CP(x): x axis,
                              then y, then z */
+  const int32_t* tri;     /* host, (N_A+N_G) triangle holding CP(x) (CPM_TRIMESH), else NULL */
 } cpm_band_info;
 
 /* Band construction (Sec. 2.1, tube-radius construction).
@@ -96,8 +106,9 @@ typedef struct {
  * 6-neighbours of actives that are not active.  Canonical order: actives lexicographic in
  * (i,j,k), k fastest, then ghosts in the same order.  Also computes each node's
  * interpolation stencil base and 1-D barycentric weights at CP_S(x) (degree p in {2,3}).
- * Errors: INVALID_ARG (h <= 0, p not 2 or 3, unknown surface), STENCIL (an interpolation
- * stencil of some node leaves the active set: lambda too small), OOM.  Host only. */
+ * Errors: INVALID_ARG (h <= 0, p not 2 or 3, unknown surface, a mesh without triangles, a
+ * vertex index out of range or a degenerate triangle), STENCIL (an interpolation stencil of
+ * some node leaves the active set: lambda too small), OOM.  Host only. */
 cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
                           cpm_band** out);
 cpm_status cpm_band_info_get(const cpm_band* band, cpm_band_info* out);
@@ -254,6 +265,19 @@ typedef struct {
  * right-hand side converged, else the first failing status. */
 cpm_status cpm_gmres_solve(const oras_precond* pc, const double* f_dev, double* u_dev, int nrhs,
                            const cpm_gmres_opts* opts, cpm_gmres_result* results, void* stream);
+
+/* (O)RAS as a stationary iterative solver (Sec. 2.2, Eq. algRAS): u_0 = 0, r_0 = f, then
+ *     u_{k+1} = u_k + M^{-1} r_k ,   r_{k+1} = f - A u_{k+1}
+ * until ||r_{k+1}||_2 <= tol ||f||_2.  Update, residual and norms are FP64; M^{-1} uses the
+ * factor precision chosen at oras_setup.  f_dev, u_dev: caller-owned device vectors of nrhs x
+ * N_A doubles (canonical band order, rhs slowest); u_dev is overwritten.  results[] has nrhs
+ * entries: iterations = preconditioner applications, relres = the true relative residual at
+ * exit, status = CPM_OK, CPM_ERR_NOT_CONVERGED (max_it reached), CPM_ERR_NAN or
+ * CPM_ERR_TIMEOUT.  A zero right-hand side returns u = 0 after 0 iterations.  Synchronises
+ * the stream once per iteration to test convergence.  Returns CPM_OK only if every
+ * right-hand side converged, else the first failing status. */
+cpm_status oras_stationary_solve(const oras_precond* pc, const double* f_dev, double* u_dev, int nrhs,
+                                 double tol, int max_it, cpm_gmres_result* results, void* stream);
 
 void oras_destroy(oras_precond* pc);
 

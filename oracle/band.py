@@ -40,6 +40,7 @@ class Band:
     grid_lo: np.ndarray      # (3,) lowest (i, j, k) of the index grid
     grid: np.ndarray         # dense int64 index grid, -1 = not a band node
     nbr: np.ndarray          # (N_A, 6) node indices of the 6 neighbours of each active
+    tri: np.ndarray | None = None   # triangle holding CP(x) per node (triangulated surfaces)
 
     @property
     def n_nodes(self) -> int:
@@ -54,6 +55,13 @@ class Band:
         out[ok] = self.grid[r[:, 0], r[:, 1], r[:, 2]]
         return out
 
+    def node_normals(self, idx: np.ndarray) -> np.ndarray:
+        """Unit surface normal at CP(x) of the given nodes: analytic for the sphere and the
+        torus, the face normal of the triangle holding CP(x) for a triangulated surface."""
+        if self.tri is not None:
+            return self.surface.normal_of(self.tri[idx])
+        return self.surface.normal(self.cp[idx])
+
     def coords(self, idx=None) -> np.ndarray:
         ijk = self.ijk if idx is None else self.ijk[idx]
         return ijk.astype(np.float64) * self.h
@@ -66,14 +74,21 @@ def _grid_range(surface, h: float, lam: float):
     return imin, imax
 
 
+def _cp_tri(surface, X: np.ndarray, dmax=None):
+    """CP(X) and, for a triangulated surface, the triangle index (else None)."""
+    if hasattr(surface, "cp_tri"):
+        return surface.cp_tri(X, dmax)
+    return surface.cp(X), None
+
+
 def _tube_test(surface, IJK: np.ndarray, h: float, lam: float):
     X = IJK.astype(np.float64) * h
-    Y = surface.cp(X)
+    Y, tri = _cp_tri(surface, X, lam)
     D = X - Y
     dist = np.sqrt((D[:, 0] * D[:, 0] + D[:, 1] * D[:, 1]) + D[:, 2] * D[:, 2])
     with np.errstate(invalid="ignore"):
         keep = dist <= lam                   # NaN (undefined CP) compares False
-    return keep, Y
+    return keep, Y, tri
 
 
 def _slab_points(i: int, imin, imax):
@@ -93,13 +108,16 @@ def active_nodes(surface, h: float, p: int, lam_over_h: float | None = None):
         lam_over_h = default_lam_over_h(p)
     lam = lam_over_h * h
     imin, imax = _grid_range(surface, h, lam)
-    ijk_parts, cp_parts = [], []
+    ijk_parts, cp_parts, tri_parts = [], [], []
     for i in range(int(imin[0]), int(imax[0]) + 1):
         IJK = _slab_points(i, imin, imax)
-        keep, Y = _tube_test(surface, IJK, h, lam)
+        keep, Y, tri = _tube_test(surface, IJK, h, lam)
         ijk_parts.append(IJK[keep])
         cp_parts.append(Y[keep])
-    return np.concatenate(ijk_parts), np.concatenate(cp_parts), lam
+        if tri is not None:
+            tri_parts.append(tri[keep])
+    tri = np.concatenate(tri_parts) if tri_parts else None
+    return np.concatenate(ijk_parts), np.concatenate(cp_parts), lam, tri
 
 
 def count_active(surface, h: float, p: int, lam_over_h: float | None = None) -> int:
@@ -108,7 +126,7 @@ def count_active(surface, h: float, p: int, lam_over_h: float | None = None) -> 
 
 
 def build_band(surface, h: float, p: int, lam_over_h: float | None = None) -> Band:
-    ijk_a, cp_a, lam = active_nodes(surface, h, p, lam_over_h)
+    ijk_a, cp_a, lam, tri_a = active_nodes(surface, h, p, lam_over_h)
     n_a = len(ijk_a)
     lo = ijk_a.min(0) - 2
     hi = ijk_a.max(0) + 2
@@ -124,10 +142,11 @@ def build_band(surface, h: float, p: int, lam_over_h: float | None = None) -> Ba
     n_g = len(ghosts)
     rg = ghosts - lo
     grid[rg[:, 0], rg[:, 1], rg[:, 2]] = n_a + np.arange(n_g)
-    cp_g = surface.cp(ghosts.astype(np.float64) * h)
+    cp_g, tri_g = _cp_tri(surface, ghosts.astype(np.float64) * h)
     ijk = np.concatenate([ijk_a, ghosts])
     cp = np.concatenate([cp_a, cp_g])
+    tri = None if tri_a is None else np.concatenate([tri_a, tri_g])
     nb = (ijk_a[:, None, :] + NBR_OFFSETS[None, :, :]) - lo
     nbr = grid[nb[..., 0], nb[..., 1], nb[..., 2]]
     assert np.all(nbr >= 0)
-    return Band(surface, h, p, lam, ijk, n_a, n_g, cp, lo, grid, nbr)
+    return Band(surface, h, p, lam, ijk, n_a, n_g, cp, lo, grid, nbr, tri)

@@ -86,7 +86,7 @@ def robin_rows(band, sub, nodes, near_cross, alpha: float, alpha_x: float):
     cols, w = interp.interpolation_rows(band, y)
     X = band.coords(nodes)
     d = X - y
-    nrm = band.surface.normal(y)
+    nrm = band.node_normals(gen)                    # normal at CP_{S_j} = CP(generator)
     dn = (d[:, 0] * nrm[:, 0] + d[:, 1] * nrm[:, 1]) + d[:, 2] * nrm[:, 2]
     dperp = d - dn[:, None] * nrm
     dq = norm3(dperp)

@@ -29,8 +29,8 @@ class OracleProblem:
 def setup(surface_kind: str, R: float, r: float, h: float, p: int, c: float, n_sub: int,
           n_overlap: int, method: str, alpha: float = 4.0, alpha_x: float = 40.0,
           leaf_weights=None, lam_over_h=None, reading: str = "R1",
-          dense: bool = False) -> OracleProblem:
-    surf = geometry.make_surface(surface_kind, R, r)
+          dense: bool = False, verts=None, tris=None) -> OracleProblem:
+    surf = geometry.make_surface(surface_kind, R, r, verts, tris)
     B = band_mod.build_band(surf, h, p, lam_over_h)
     E = interp.extension_matrix(B)
     A = operator.cpm_matrix(B, E, c)
@@ -50,7 +50,11 @@ def setup(surface_kind: str, R: float, r: float, h: float, p: int, c: float, n_s
 
 
 def setup_workload(wl, **kw) -> OracleProblem:
-    from workloads import leaf_weights, rhs
+    from workloads import leaf_weights, rhs, surface_mesh
+    mesh = surface_mesh(wl)
+    if mesh is not None:
+        kw.setdefault("verts", mesh[0])
+        kw.setdefault("tris", mesh[1])
     prob = setup(wl.surface, wl.R, wl.r, wl.h, wl.p, wl.c, wl.n_sub, wl.n_overlap, wl.method,
                  wl.alpha, wl.alpha_x, leaf_weights(wl.n_sub, wl.weight_seed), **kw)
     prob.f = rhs(wl, prob.band.cp[:prob.band.n_active])

@@ -15,11 +15,12 @@ import numpy as np
 from . import _capi
 from ._capi import (CPM_BF16, CPM_FP32, CPM_FP64, CPM_ORAS, CPM_ORAS_R3, CPM_RAS,  # noqa: F401
                     CPM_SET_BC_A, CPM_SET_BC_G, CPM_SET_BC_GEN, CPM_SET_BC_NEARX, CPM_SET_GHOST,
-                    CPM_SET_LAST, CPM_SET_OWN, CPM_SET_SIGMA, CPM_SPHERE, CPM_TORUS)
+                    CPM_SET_LAST, CPM_SET_OWN, CPM_SET_SIGMA, CPM_SPHERE, CPM_TORUS,
+                    CPM_TRIMESH)
 
 PRECISIONS = {"fp64": CPM_FP64, "fp32": CPM_FP32, "bf16": CPM_BF16}
 TRANSMISSIONS = {"ras": CPM_RAS, "oras": CPM_ORAS, "oras_r3": CPM_ORAS_R3}
-SURFACES = {"sphere": CPM_SPHERE, "torus": CPM_TORUS}
+SURFACES = {"sphere": CPM_SPHERE, "torus": CPM_TORUS, "trimesh": CPM_TRIMESH}
 
 
 class CpmError(RuntimeError):
@@ -78,6 +79,7 @@ class Band:
             "base": arr(inf.base, 3 * n, np.int64).reshape(n, 3),
             "pencil": arr(inf.pencil, n * (inf.p + 1) ** 2, np.int32).reshape(n, (inf.p + 1) ** 2),
             "weights": arr(inf.weights, n * 3 * (inf.p + 1), np.float64).reshape(n, 3, inf.p + 1),
+            "tri": arr(inf.tri, n, np.int64) if inf.tri else None,
         }
 
 
@@ -153,8 +155,18 @@ class Preconditioner:
 
 # ---------------------------------------------------------------- entry points
 def cpm_build_band(surface: str, R: float, r: float, h: float, p: int,
-                   lambda_over_h: float = 0.0) -> Band:
+                   lambda_over_h: float = 0.0, verts=None, tris=None) -> Band:
+    """Band of a sphere / torus (R, r) or of a triangulated surface (verts (n,3), tris (m,3))."""
     s = _capi.cpm_surface(SURFACES[surface], float(R), float(r))
+    if surface == "trimesh":
+        V = np.ascontiguousarray(verts, dtype=np.float64)
+        T = np.ascontiguousarray(tris, dtype=np.int32)
+        if V.ndim != 2 or V.shape[1] != 3 or T.ndim != 2 or T.shape[1] != 3:
+            raise ValueError("cpm_build_band: verts (n,3) and tris (m,3) expected")
+        s.verts = V.ctypes.data_as(C.POINTER(C.c_double))
+        s.n_verts = V.shape[0]
+        s.tris = T.ctypes.data_as(C.POINTER(C.c_int32))
+        s.n_tris = T.shape[0]
     h_out = C.c_void_p()
     _check(_capi.load().cpm_build_band(C.byref(s), float(h), int(p), float(lambda_over_h),
                                        C.byref(h_out)), "cpm_build_band")
@@ -272,6 +284,20 @@ def cpm_gmres_solve(pc: Preconditioner, f, u, nrhs: int = 1, restart: int = 50, 
     out = [{"iterations": r.iterations, "relres": r.relres, "status": r.status} for r in res]
     if st != 0 and (raise_on_failure or st not in (_capi.CPM_ERR_NOT_CONVERGED,)):
         raise CpmError(st, "cpm_gmres_solve")
+    return out
+
+
+def oras_stationary_solve(pc: Preconditioner, f, u, nrhs: int = 1, tol: float = 1e-8,
+                          max_it: int = 1000, stream=None, raise_on_failure: bool = True):
+    """(O)RAS as a solver, u <- u + M^{-1}(f - A u) (Eq. algRAS).  List of dicts per rhs."""
+    n = pc.n_active * nrhs
+    res = (_capi.cpm_gmres_result * nrhs)()
+    st = _capi.load().oras_stationary_solve(pc.handle, _dev_ptr(f, n, "f"), _dev_ptr(u, n, "u"),
+                                            int(nrhs), float(tol), int(max_it), res,
+                                            _stream_ptr(stream))
+    out = [{"iterations": r.iterations, "relres": r.relres, "status": r.status} for r in res]
+    if st != 0 and (raise_on_failure or st not in (_capi.CPM_ERR_NOT_CONVERGED,)):
+        raise CpmError(st, "oras_stationary_solve")
     return out
 
 

@@ -20,7 +20,7 @@ CPM_ERR_TIMEOUT = 8
 CPM_ERR_BUDGET = 9
 CPM_ERR_STENCIL = 10
 # enums
-CPM_SPHERE, CPM_TORUS = 0, 1
+CPM_SPHERE, CPM_TORUS, CPM_TRIMESH = 0, 1, 2
 CPM_TUNE_SOLVE_CTAS_PER_SM, CPM_TUNE_SOLVE_KSEG, CPM_TUNE_SOLVE_PREFETCH, CPM_TUNE_SOLVE_STAGGER = 0, 1, 2, 3
 CPM_RAS, CPM_ORAS, CPM_ORAS_R3 = 0, 1, 2
 CPM_FP64, CPM_FP32, CPM_BF16 = 0, 1, 2
@@ -30,14 +30,17 @@ CPM_SETUP_SIMT_LU = 0x100
 
 
 class cpm_surface(C.Structure):
-    _fields_ = [("kind", C.c_int), ("R", C.c_double), ("r", C.c_double)]
+    _fields_ = [("kind", C.c_int), ("R", C.c_double), ("r", C.c_double),
+                ("verts", C.POINTER(C.c_double)), ("n_verts", C.c_int64),
+                ("tris", C.POINTER(C.c_int32)), ("n_tris", C.c_int64)]
 
 
 class cpm_band_info(C.Structure):
     _fields_ = [("n_active", C.c_int64), ("n_ghost", C.c_int64), ("p", C.c_int), ("h", C.c_double),
                 ("lambda_", C.c_double), ("ijk", C.POINTER(C.c_int32)), ("cp", C.POINTER(C.c_double)),
                 ("nbr", C.POINTER(C.c_int32)), ("base", C.POINTER(C.c_int32)),
-                ("pencil", C.POINTER(C.c_int32)), ("weights", C.POINTER(C.c_double))]
+                ("pencil", C.POINTER(C.c_int32)), ("weights", C.POINTER(C.c_double)),
+                ("tri", C.POINTER(C.c_int32))]
 
 
 class oras_info(C.Structure):
@@ -85,6 +88,8 @@ _SIGS = {
     "oras_autotune": (C.c_int, [_P, _P]),
     "cpm_gmres_solve": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(cpm_gmres_opts),
                                   C.POINTER(cpm_gmres_result), _P]),
+    "oras_stationary_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_int,
+                                        C.POINTER(cpm_gmres_result), _P]),
     "oras_destroy": (None, [_P]),
     "cpm_status_string": (C.c_char_p, [C.c_int]),
     "cpm_last_error": (C.c_char_p, []),

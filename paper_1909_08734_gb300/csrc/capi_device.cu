@@ -1,6 +1,7 @@
 // C ABI: entry points that run on the GPU (preconditioner setup, operator apply,
 // preconditioner apply, FGMRES).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -88,6 +89,10 @@ struct oras_precond {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t iter_graph = nullptr;
   int graph_m = 0;
+  // stationary solver workspace
+  double *st_z = nullptr, *st_r = nullptr, *st_part = nullptr, *st_norm = nullptr;
+  double* st_norm_host = nullptr;
+  int st_nblk = 0;
 
   void* alloc(size_t bytes, cudaError_t* err) {
     void* p = nullptr;
@@ -116,6 +121,7 @@ struct oras_precond {
     for (auto& b : bufs) cudaFree(b.p);
     if (g_state_host) cudaFreeHost(g_state_host);
     if (g_istate_host) cudaFreeHost(g_istate_host);
+    if (st_norm_host) cudaFreeHost(st_norm_host);
     if (cur >= 0) cudaSetDevice(cur);
   }
 };
@@ -530,6 +536,74 @@ cpm_status capture_graph(oras_precond* pc) {
   return CPM_OK;
 }
 
+cpm_status ensure_stationary(oras_precond* pc) {
+  if (pc->st_z) return CPM_OK;
+  const int64_t n = pc->n_active;
+  pc->st_nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(pc->device)));
+  ALLOC(pc->st_z, double, n);
+  ALLOC(pc->st_r, double, n);
+  ALLOC(pc->st_part, double, pc->st_nblk);
+  ALLOC(pc->st_norm, double, 2);
+  if (!pc->st_norm_host) CK(cudaMallocHost(&pc->st_norm_host, 2 * sizeof(double)));
+  if (!pc->g_vext) ALLOC(pc->g_vext, double, pc->n_nodes);
+  return CPM_OK;
+}
+
+// ||x||_2 on the device, returned to the host (one synchronisation).
+cpm_status norm_to_host(oras_precond* pc, const double* x, int slot, double* out, cudaStream_t s) {
+  CK(launch_norm2(x, pc->n_active, pc->st_part, pc->st_nblk, pc->st_norm + slot, s));
+  CK(cudaMemcpyAsync(pc->st_norm_host + slot, pc->st_norm + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  pc->launches += KERNELS_NORM2;
+  *out = pc->st_norm_host[slot];
+  return CPM_OK;
+}
+
+cpm_status stationary_one(oras_precond* pc, const double* f, double* u, double tol, int max_it,
+                          cpm_gmres_result* res, cudaStream_t s) {
+  const int64_t n = pc->n_active;
+  res->iterations = 0;
+  res->relres = 0.0;
+  res->status = CPM_OK;
+  CK(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
+  double nf = 0.0;
+  cpm_status st = norm_to_host(pc, f, 0, &nf, s);
+  if (st != CPM_OK) return st;
+  if (!std::isfinite(nf)) {
+    res->status = CPM_ERR_NAN;
+    return CPM_OK;
+  }
+  if (nf == 0.0) return CPM_OK;
+  CK(cudaMemcpyAsync(pc->st_r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  res->status = CPM_ERR_NOT_CONVERGED;
+  for (int it = 1; it <= max_it; ++it) {
+    CK(launch_trsv(pc->trsv, direct(pc->st_r, 0), direct(pc->st_z, 0), nullptr, s));
+    CK(launch_axpy(u, pc->st_z, n, pc->st_nblk, s));
+    CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(pc->st_r, 0), 1, 1, nullptr, s));
+    pc->launches += KERNELS_TRSV + KERNELS_AXPY + KERNELS_APPLY;
+    double nr = 0.0;
+    st = norm_to_host(pc, pc->st_r, 1, &nr, s);
+    if (st != CPM_OK) return st;
+    res->iterations = it;
+    res->relres = nr / nf;
+    if (!std::isfinite(nr)) {
+      res->status = CPM_ERR_NAN;
+      break;
+    }
+    if (nr <= tol * nf) {
+      res->status = CPM_OK;
+      break;
+    }
+  }
+  int dst = 0;
+  CK(cudaMemcpy(&dst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (dst & ST_TIMEOUT) {
+    CK(cudaMemset(pc->status, 0, sizeof(int)));
+    res->status = CPM_ERR_TIMEOUT;
+  }
+  return CPM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -744,6 +818,26 @@ cpm_status cpm_gmres_solve(const oras_precond* cpc, const double* f_dev, double*
   }
   if (had_graph) pc->iter_graph = saved;
   if (first != CPM_OK) cpm::set_error(std::string("cpm_gmres_solve: ") + cpm_status_string(first));
+  return first;
+}
+
+cpm_status oras_stationary_solve(const oras_precond* cpc, const double* f_dev, double* u_dev, int nrhs,
+                                 double tol, int max_it, cpm_gmres_result* results, void* stream) {
+  oras_precond* pc = const_cast<oras_precond*>(cpc);
+  if (!pc || !f_dev || !u_dev || nrhs < 1 || !results || !(tol > 0.0) || max_it < 1) {
+    cpm::set_error("oras_stationary_solve: bad argument (need tol > 0, max_it >= 1)");
+    return CPM_ERR_INVALID_ARG;
+  }
+  cpm_status st = ensure_stationary(pc);
+  if (st != CPM_OK) return st;
+  cpm_status first = CPM_OK;
+  for (int i = 0; i < nrhs; ++i) {
+    st = stationary_one(pc, f_dev + (int64_t)i * pc->n_active, u_dev + (int64_t)i * pc->n_active, tol, max_it,
+                        &results[i], (cudaStream_t)stream);
+    if (st != CPM_OK) return st;
+    if (first == CPM_OK && results[i].status != CPM_OK) first = (cpm_status)results[i].status;
+  }
+  if (first != CPM_OK) cpm::set_error(std::string("oras_stationary_solve: ") + cpm_status_string(first));
   return first;
 }
 

@@ -39,8 +39,21 @@ cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double la
   }
   *out = nullptr;
   try {
+    cpm::Surface s{surface->kind, surface->R, surface->r, {}};
+    if (s.kind == CPM_TRIMESH) {
+      if (!surface->verts || !surface->tris || surface->n_verts < 3 || surface->n_tris < 1) {
+        cpm::set_error("cpm_build_band: a triangulated surface needs vertices and triangles");
+        return CPM_ERR_INVALID_ARG;
+      }
+      s.mesh.V.assign(surface->verts, surface->verts + 3 * surface->n_verts);
+      s.mesh.T.assign(surface->tris, surface->tris + 3 * surface->n_tris);
+      for (int32_t v : s.mesh.T)
+        if (v < 0 || v >= surface->n_verts) {
+          cpm::set_error("cpm_build_band: triangle vertex index out of range");
+          return CPM_ERR_INVALID_ARG;
+        }
+    }
     cpm_band* b = new cpm_band();
-    cpm::Surface s{surface->kind, surface->R, surface->r};
     cpm_status st = cpm::build_band(s, h, p, lambda_over_h, b->b);
     if (st != CPM_OK) {
       delete b;
@@ -71,6 +84,7 @@ cpm_status cpm_band_info_get(const cpm_band* band, cpm_band_info* out) {
   out->base = B.base.data();
   out->pencil = B.pencil.data();
   out->weights = B.wts.data();
+  out->tri = B.tri.empty() ? nullptr : B.tri.data();
   return CPM_OK;
 }
 

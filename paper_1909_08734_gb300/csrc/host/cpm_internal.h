@@ -13,16 +13,35 @@ namespace cpm {
 
 void set_error(const std::string& msg);
 
+// Triangulated surface with a uniform bucket grid over the triangles' bounding boxes.
+struct Mesh {
+  std::vector<double> V;          // n_verts x 3
+  std::vector<int32_t> T;         // n_tris x 3
+  std::vector<double> fn;         // n_tris x 3 unit face normals
+  double org[3] = {0, 0, 0}, cell = 0;
+  int32_t nc[3] = {0, 0, 0};      // cells per axis
+  std::vector<int64_t> cell_start;  // CSR over cells of triangle lists (ascending index)
+  std::vector<int32_t> cell_tris;
+  int64_t n_tris() const { return (int64_t)T.size() / 3; }
+};
+
 struct Surface {
   int kind;
   double R, r;
+  Mesh mesh;                      // CPM_TRIMESH only
 };
 
 // Closest point (Sec. 2.1). Returns false where CP is undefined (sphere centre, torus axis
 // or ring circle); such points are never band nodes.
 bool closest_point(const Surface& s, const double x[3], double y[3]);
-// Unit surface normal at a surface point y.
+// Unit surface normal at a surface point y (analytic surfaces).
 void surface_normal(const Surface& s, const double y[3], double n[3]);
+// Mesh: validates the triangles, computes face normals and the bucket grid (cell size s).
+cpm_status mesh_prepare(Mesh& m, double cell);
+// Exact closest point over all triangles (ties: lowest index) if it lies within dmax of x;
+// returns the triangle index, or -1 if every triangle is farther than dmax.
+int32_t mesh_closest_point(const Mesh& m, const double x[3], double dmax, double y[3],
+                           std::vector<int32_t>& stamp, int32_t& qid);
 
 // 1-D barycentric Lagrange weights on nodes 0..p at offset t (Sec. 2.1, second form).
 void bary_weights(double t, int p, double* w);
@@ -41,6 +60,7 @@ struct Band {
   std::vector<int32_t> base;     // N x 3 stencil bases of CP(x)
   std::vector<double> wts;       // N x 3 x (p+1) 1-D weights (x, then y, then z)
   std::vector<int32_t> pencil;   // N x (p+1)^2 first active index of each z-pencil
+  std::vector<int32_t> tri;      // N triangle holding CP(x) (meshes only)
   int32_t lo[3] = {0, 0, 0}, dims[3] = {0, 0, 0};
   std::vector<int32_t> grid;     // dense index grid, -1 = no node
   int64_t n_nodes() const { return n_active + n_ghost; }
@@ -56,6 +76,9 @@ struct Band {
   mutable void* d_nbr = nullptr;
   mutable int d_device = -1;
 };
+
+// Unit surface normal at CP(x) of node g (analytic, or the face normal of its triangle).
+void node_normal(const Band& B, int64_t g, double n[3]);
 
 struct SubSets {
   std::vector<int32_t> own, sigma, last, ghost, bc_a, bc_g;

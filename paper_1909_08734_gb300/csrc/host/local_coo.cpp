@@ -119,7 +119,7 @@ cpm_status build_local_coo(const Band& B, const Partition& part, double c, int t
       double x[3] = {(double)B.ijk[3 * (size_t)g] * h, (double)B.ijk[3 * (size_t)g + 1] * h,
                      (double)B.ijk[3 * (size_t)g + 2] * h};
       double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]}, nv[3];
-      surface_normal(B.surf, y, nv);
+      node_normal(B, S.bc_gen[t], nv);          // normal at CP_{S_j} = CP(generator)
       double dn = (d[0] * nv[0] + d[1] * nv[1]) + d[2] * nv[2];
       double dp[3] = {d[0] - dn * nv[0], d[1] - dn * nv[1], d[2] - dn * nv[2]};
       double dq = std::sqrt((dp[0] * dp[0] + dp[1] * dp[1]) + dp[2] * dp[2]);

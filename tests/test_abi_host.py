@@ -10,6 +10,7 @@ import paper_1909_08734_gb300 as G
 from paper_1909_08734_gb300 import _capi
 from oracle import band as ob
 from oracle import geometry, interp, local, operator, partition
+from workloads import perturbed_icosphere
 
 HDR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "cpm.h")
 
@@ -54,15 +55,22 @@ def test_invalid_arguments_are_reported():
 CASES = [("sphere", 1.0, 0.0, 0.1, 3, 8, 2, None),
          ("sphere", 1.0, 0.0, 0.1, 2, 6, 3, None),
          ("torus", 1.0, 0.4, 0.05, 3, 16, 2, [256, 1024, 300, 500, 999, 700, 260, 800,
-                                             400, 410, 420, 1000, 256, 257, 900, 333])]
+                                             400, 410, 420, 1000, 256, 257, 900, 333]),
+         ("trimesh", 0.0, 0.0, 0.05, 3, 8, 2, None)]
+
+
+def _mesh(kind):
+    # the small perturbed icosphere (3 subdivisions, 1,280 triangles)
+    return perturbed_icosphere(3, 0.15, 4) if kind == "trimesh" else (None, None)
 
 
 @pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-h{c[3]}-p{c[4]}-S{c[5]}")
 def pair(request):
     kind, R, r, h, p, ns, no, w = request.param
-    band = G.cpm_build_band(kind, R, r, h, p)
+    V, T = _mesh(kind)
+    band = G.cpm_build_band(kind, R, r, h, p, verts=V, tris=T)
     part = G.cpm_partition(band, ns, w, no)
-    OB = ob.build_band(geometry.make_surface(kind, R, r), h, p)
+    OB = ob.build_band(geometry.make_surface(kind, R, r, V, T), h, p)
     E = interp.extension_matrix(OB)
     lab = partition.rcb(OB.cp[:OB.n_active], ns, w)
     return band, part, OB, E, lab, ns, no
@@ -75,6 +83,10 @@ def test_band_bit_exact(pair):
     assert np.array_equal(inf["ijk"], OB.ijk)
     assert np.array_equal(inf["cp"], OB.cp)
     assert np.array_equal(inf["nbr"], OB.nbr)
+    if OB.tri is not None:
+        assert np.array_equal(inf["tri"], OB.tri)
+    else:
+        assert inf["tri"] is None
     base, _ = interp.stencil_base(OB.cp, OB.h, OB.p)
     assert np.array_equal(inf["base"], base)
 
