@@ -179,8 +179,30 @@ typedef struct {
   int solve_kseg;
   int solve_prefetch;
   int solve_stagger;
+  int64_t peak_device_bytes;  /* largest device_bytes reached so far (setup included) */
 } oras_info;
 cpm_status oras_info_get(const oras_precond* pc, oras_info* out);
+/* Device-memory plan of an oras_setup call, computed on the host without touching a GPU
+ * (admission control of the serving loop).  No counterpart in the paper.
+ *   setup_peak_bytes : upper bound of the device bytes held during oras_setup (band copies,
+ *                      assembly buffers, factor work tiles, diagonal-block inverses);
+ *   resident_bytes   : upper bound of the bytes held afterwards by the handle once it has
+ *                      run cpm_gmres_solve with this restart length and cpm_op_apply /
+ *                      oras_apply with up to nrhs right-hand sides (any solve schedule);
+ *   factor_bytes     : exact bytes of the resident factors;
+ *   vector_bytes     : bytes of nrhs right-hand sides and solutions (f, u: 2 nrhs N_A 8),
+ *                      caller-owned, reported for budgeting.
+ * Bounds include a per-allocation rounding allowance.  Errors: INVALID_ARG. */
+typedef struct {
+  int64_t setup_peak_bytes;
+  int64_t resident_bytes;
+  int64_t factor_bytes;
+  int64_t vector_bytes;
+  int64_t sum_n2;
+  int max_tiles;            /* largest number of 64-row tiles per dimension */
+} oras_plan_info;
+cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmission, int precision,
+                     int restart, int nrhs, oras_plan_info* out);
 /* Schedule knobs of the batched local solve (oras_apply and the solves inside
  * cpm_gmres_solve).  They change speed only, never results beyond rounding order:
  *   CPM_TUNE_SOLVE_CTAS_PER_SM  persistent CTAs per SM (1 .. shared-memory limit)
@@ -278,6 +300,12 @@ cpm_status cpm_gmres_solve(const oras_precond* pc, const double* f_dev, double* 
  * right-hand side converged, else the first failing status. */
 cpm_status oras_stationary_solve(const oras_precond* pc, const double* f_dev, double* u_dev, int nrhs,
                                  double tol, int max_it, cpm_gmres_result* results, void* stream);
+
+/* y = a x + b y on the device (b == 0: y = a x and y is not read), n doubles, asynchronous on
+ * the stream.  A utility for drivers above the solver (for example a backward-Euler chain
+ * whose next right-hand side is u_n / dt); no counterpart in the paper.  Errors:
+ * INVALID_ARG (n < 0, NULL pointers with n > 0), CUDA. */
+cpm_status cpm_vec_axpby(int64_t n, double a, const double* x_dev, double b, double* y_dev, void* stream);
 
 void oras_destroy(oras_precond* pc);
 

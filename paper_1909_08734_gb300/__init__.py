@@ -218,6 +218,16 @@ def oras_setup(band: Band, part: Partition, c: float, transmission: str = "oras"
     return Preconditioner(h_out, band, part)
 
 
+def oras_plan(band: Band, part: Partition, transmission: str = "oras", precision: str = "fp64",
+              restart: int = 50, nrhs: int = 1) -> dict:
+    """Host-side device-memory plan of oras_setup + solves (bytes); touches no GPU."""
+    out = _capi.oras_plan_info()
+    _check(_capi.load().oras_plan(band.handle, part.handle, TRANSMISSIONS[transmission],
+                                  PRECISIONS[precision], int(restart), int(nrhs), C.byref(out)),
+           "oras_plan")
+    return {f: getattr(out, f) for f, _ in _capi.oras_plan_info._fields_}
+
+
 def cpm_op_apply(pc: Preconditioner, x, y, nrhs: int = 1, stream=None):
     n = pc.n_active * nrhs
     _check(_capi.load().cpm_op_apply(pc.handle, _dev_ptr(x, n, "x"), _dev_ptr(y, n, "y"), int(nrhs),
@@ -299,6 +309,13 @@ def oras_stationary_solve(pc: Preconditioner, f, u, nrhs: int = 1, tol: float = 
     if st != 0 and (raise_on_failure or st not in (_capi.CPM_ERR_NOT_CONVERGED,)):
         raise CpmError(st, "oras_stationary_solve")
     return out
+
+
+def cpm_vec_axpby(a: float, x, b: float, y, n: int | None = None, stream=None):
+    """y = a x + b y on the device (b == 0: y = a x)."""
+    n = y.numel() if n is None else int(n)
+    _check(_capi.load().cpm_vec_axpby(n, float(a), _dev_ptr(x, n, "x"), float(b), _dev_ptr(y, n, "y"),
+                                      _stream_ptr(stream)), "cpm_vec_axpby")
 
 
 def status_string(code: int) -> str:

@@ -50,7 +50,14 @@ class oras_info(C.Structure):
                 ("factor_bytes", C.c_int64), ("device_bytes", C.c_int64),
                 ("setup_ms_assemble", C.c_double), ("setup_ms_factor", C.c_double),
                 ("kernel_launches", C.c_int64), ("solve_ctas_per_sm", C.c_int),
-                ("solve_kseg", C.c_int), ("solve_prefetch", C.c_int), ("solve_stagger", C.c_int)]
+                ("solve_kseg", C.c_int), ("solve_prefetch", C.c_int), ("solve_stagger", C.c_int),
+                ("peak_device_bytes", C.c_int64)]
+
+
+class oras_plan_info(C.Structure):
+    _fields_ = [("setup_peak_bytes", C.c_int64), ("resident_bytes", C.c_int64),
+                ("factor_bytes", C.c_int64), ("vector_bytes", C.c_int64), ("sum_n2", C.c_int64),
+                ("max_tiles", C.c_int)]
 
 
 class cpm_gmres_opts(C.Structure):
@@ -78,6 +85,7 @@ _SIGS = {
     "oras_setup": (C.c_int, [_P, _P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _P,
                              C.POINTER(_P)]),
     "oras_info_get": (C.c_int, [_P, C.POINTER(oras_info)]),
+    "oras_plan": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(oras_plan_info)]),
     "oras_local_sizes": (C.c_int, [_P, _P]),
     "cpm_op_apply": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "cpm_op_apply_noalloc": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int64, C.c_int, C.c_double,
@@ -90,6 +98,7 @@ _SIGS = {
                                   C.POINTER(cpm_gmres_result), _P]),
     "oras_stationary_solve": (C.c_int, [_P, _P, _P, C.c_int, C.c_double, C.c_int,
                                         C.POINTER(cpm_gmres_result), _P]),
+    "cpm_vec_axpby": (C.c_int, [C.c_int64, C.c_double, _P, C.c_double, _P, _P]),
     "oras_destroy": (None, [_P]),
     "cpm_status_string": (C.c_char_p, [C.c_int]),
     "cpm_last_error": (C.c_char_p, []),

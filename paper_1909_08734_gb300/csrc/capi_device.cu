@@ -68,7 +68,7 @@ struct oras_precond {
   int64_t launches = 0;       // kernels launched after setup (graph nodes included)
   int solve_ctas = 0;         // current CTAs per SM of the batched solve
   std::vector<DevBuf> bufs;
-  size_t device_bytes = 0, factor_bytes = 0;
+  size_t device_bytes = 0, factor_bytes = 0, peak_bytes = 0;
   // device pointers
   void* tiles = nullptr;      // factors used by the solves
   void* dinv = nullptr;
@@ -100,6 +100,7 @@ struct oras_precond {
     if (*err == cudaSuccess) {
       bufs.push_back({p, bytes});
       device_bytes += bytes;
+      peak_bytes = std::max(peak_bytes, device_bytes);
     }
     return p;
   }
@@ -664,6 +665,73 @@ cpm_status oras_info_get(const oras_precond* pc, oras_info* o) {
   o->solve_kseg = pc->trsv.kseg;
   o->solve_prefetch = pc->trsv.prefetch;
   o->solve_stagger = pc->trsv.stagger;
+  o->peak_device_bytes = (int64_t)pc->peak_bytes;
+  return CPM_OK;
+}
+
+cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmission, int precision,
+                     int restart, int nrhs, oras_plan_info* out) {
+  if (!band || !part || !out || restart < 1 || nrhs < 1 ||
+      (precision != CPM_FP64 && precision != CPM_FP32 && precision != CPM_BF16) ||
+      (transmission != CPM_RAS && transmission != CPM_ORAS && transmission != CPM_ORAS_R3)) {
+    cpm::set_error("oras_plan: bad argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  const cpm::Band& B = band->b;
+  const cpm::Partition& P = part->p;
+  if (P.band != &B) {
+    cpm::set_error("oras_plan: partition of another band");
+    return CPM_ERR_INVALID_ARG;
+  }
+  const int ns = P.n_sub;
+  const int64_t N = B.n_active, NN = B.n_nodes();
+  const int64_t P3 = (int64_t)B.P() * B.P() * B.P();
+  const int64_t wb = precision == CPM_FP64 ? 8 : 4;
+  int64_t tile_elems = 0, rows = 0, sum_n = 0, sum_n2 = 0, nnz_bound = 0;
+  int t_max = 0;
+  std::vector<int> Ts(ns);
+  for (int j = 0; j < ns; ++j) {
+    const cpm::SubSets& S = P.subs[j];
+    const int64_t n = (int64_t)S.sigma.size() + (transmission != CPM_RAS ? (int64_t)S.bc_a.size() : 0);
+    const int T = (int)((n + TILE - 1) / TILE);
+    Ts[j] = T;
+    t_max = std::max(t_max, T);
+    tile_elems += (int64_t)T * T * TILE_ELEMS;
+    rows += (int64_t)T * TILE;
+    sum_n += n;
+    sum_n2 += n * n;
+    nnz_bound += n * (1 + 6 * P3);
+  }
+  // every allocation may be rounded up to a 2 MiB page
+  const int64_t page = 2 << 20;
+  auto rnd = [&](int64_t b) { return ((b + page - 1) / page) * page; };
+  const int64_t band_dev = rnd(4 * NN * B.P() * B.P()) + rnd(8 * NN * 3 * B.P()) + rnd(4 * N * 6);
+  const int64_t work = rnd(wb * tile_elems);
+  const int64_t inv = rnd(2 * wb * rows * TILE);
+  const int64_t small = rnd(sizeof(SubMeta) * ns) + 2 * rnd(4 * rows) + rnd(4) + rnd(16);
+  const int64_t assembly = rnd(4 * rows) /* pivots */ + rnd(wb * rows) /* dinv */ + 2 * rnd(4 * sum_n) +
+                           rnd(8 * ns) + rnd(8 * nnz_bound) + rnd(8 * nnz_bound);
+  const int64_t factor = precision == CPM_BF16 ? 2 * tile_elems : wb * tile_elems;
+  // batched-solve schedule: the autotuner's smallest split (8 tiles) needs the most slots
+  std::vector<int2> items;
+  int maxseg = 1;
+  trsv_build_items(Ts.data(), ns, 8, 0, items, &maxseg);
+  const int words = precision == CPM_FP64 ? 2 : 1;
+  const int64_t sched = rnd(8 * (int64_t)items.size()) + rnd(8 * words * (rows / TILE) * maxseg * TILE) +
+                        rnd(8 * words * rows) + rnd(16);
+  const int64_t nblk = 152;
+  const int64_t gmres = rnd(8 * (restart + 1) * N) + rnd(8 * restart * N) + 2 * rnd(8 * N) +
+                        rnd(8 * nblk * (restart + 2)) + rnd(8 * (int64_t)(restart + 2) * (restart + 8) + 4096) +
+                        rnd(64) + rnd(8 * NN) /* extension values */ + rnd(8 * nrhs * NN) /* apply scratch */;
+  const int64_t setup_peak = band_dev + work + inv + small + assembly +
+                             (precision == CPM_BF16 ? rnd(2 * tile_elems) : 0);
+  const int64_t resident = band_dev + rnd(factor) + inv + small + sched + gmres;
+  out->setup_peak_bytes = setup_peak + (setup_peak >> 6);
+  out->resident_bytes = resident + (resident >> 6);
+  out->factor_bytes = factor;
+  out->vector_bytes = 2 * 8 * (int64_t)nrhs * N;
+  out->sum_n2 = sum_n2;
+  out->max_tiles = t_max;
   return CPM_OK;
 }
 
@@ -839,6 +907,19 @@ cpm_status oras_stationary_solve(const oras_precond* cpc, const double* f_dev, d
   }
   if (first != CPM_OK) cpm::set_error(std::string("oras_stationary_solve: ") + cpm_status_string(first));
   return first;
+}
+
+cpm_status cpm_vec_axpby(int64_t n, double a, const double* x_dev, double b, double* y_dev, void* stream) {
+  if (n < 0 || (n > 0 && (!x_dev || !y_dev))) {
+    cpm::set_error("cpm_vec_axpby: bad argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  if (n == 0) return CPM_OK;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4 * (int64_t)sm_count(dev)));
+  CK(launch_axpby(n, a, x_dev, b, y_dev, nblk, (cudaStream_t)stream));
+  return CPM_OK;
 }
 
 void oras_destroy(oras_precond* pc) { delete pc; }

@@ -48,6 +48,7 @@ constexpr int KERNELS_AXPY = 1;
 constexpr int KERNELS_NORM2 = 2;
 cudaError_t launch_axpy(double* u, const double* z, int64_t n, int nblk, cudaStream_t s);
 cudaError_t launch_norm2(const double* x, int64_t n, double* partial, int nblk, double* out, cudaStream_t s);
+cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, int nblk, cudaStream_t s);
 
 cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
                          IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s);

@@ -43,6 +43,18 @@ __global__ void norm_finish_kernel(const double* __restrict__ partial, int nblk,
   *out = sqrt(t);
 }
 
+// y = a x + b y (b == 0: y = a x, without reading y)
+__global__ void __launch_bounds__(ST_THREADS) axpby_kernel(int64_t n, double a, const double* __restrict__ x,
+                                                           double b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)ST_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * ST_THREADS)
+    y[i] = b == 0.0 ? a * x[i] : a * x[i] + b * y[i];
+}
+
+cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, int nblk, cudaStream_t s) {
+  axpby_kernel<<<nblk, ST_THREADS, 0, s>>>(n, a, x, b, y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_axpy(double* u, const double* z, int64_t n, int nblk, cudaStream_t s) {
   axpy_kernel<<<nblk, ST_THREADS, 0, s>>>(u, z, n);
   return cudaGetLastError();

@@ -221,3 +221,57 @@ def poisson_arrivals(n_req: int, rate_per_s: float, seed: int = 5) -> np.ndarray
     """Arrival times (s) of a Poisson request stream."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n_req))
+
+
+# ---------------------------------------------------------------- serving stream
+SERVING_SURFACES = ("sphere", "torus", "mesh")
+SERVING_H = (0.05, 0.025, 0.0125)
+SERVING_H_PROB = (0.5, 0.35, 0.15)
+
+
+@dataclasses.dataclass(frozen=True)
+class ServingRequestSpec:
+    """One request of the serving stream: operator (surface, h, c), right-hand sides and an
+    optional backward-Euler chain (c = 1/dt, rhs_{n+1} = u_n / dt, same factorisation)."""
+    rid: int
+    surface: str            # "sphere" | "torus" | "mesh" (the 81,920-triangle workload mesh)
+    h: float
+    c: float
+    nrhs: int
+    rhs_seed: int
+    chain_steps: int        # backward-Euler steps after the first solve (0: plain solve)
+
+
+def serving_stream(n_req: int, seed: int = 5, repeat_prob: float = 0.3, chain_prob: float = 0.25,
+                   max_nrhs: int = 32, h_choices=SERVING_H, h_prob=SERVING_H_PROB):
+    """Seeded request mix: surface uniform over sphere / torus(1, 0.4) / perturbed-icosphere
+    mesh, h from h_choices with probabilities h_prob, c log-uniform in [0.1, 100], 1..max_nrhs
+    smooth right-hand sides (log-uniform), a fraction of backward-Euler chains (2-6 steps, one
+    rhs) and a fraction of requests that reuse an earlier request's operator (same surface, h
+    and c), which is what lets factorisations and batches be shared."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_req):
+        if out and rng.uniform() < repeat_prob:
+            prev = out[int(rng.integers(0, len(out)))]
+            surface, h, c = prev.surface, prev.h, prev.c
+        else:
+            surface = SERVING_SURFACES[int(rng.integers(0, len(SERVING_SURFACES)))]
+            h = float(h_choices[int(rng.choice(len(h_choices), p=np.asarray(h_prob) / np.sum(h_prob)))])
+            c = float(10.0 ** rng.uniform(-1.0, 2.0))
+        if rng.uniform() < chain_prob:
+            nrhs, steps = 1, int(rng.integers(2, 7))
+        else:
+            nrhs = int(min(max_nrhs, np.floor(np.exp(rng.uniform(0.0, math.log(max_nrhs + 1))))))
+            nrhs, steps = max(1, nrhs), 0
+        out.append(ServingRequestSpec(i, surface, h, c, nrhs, int(rng.integers(0, 2 ** 31)), steps))
+    return out
+
+
+def smooth_rhs(Y: np.ndarray, seed: int, nrhs: int) -> np.ndarray:
+    """nrhs smooth right-hand sides (8 ambient modes each, std 1) at surface points Y."""
+    F = np.empty((nrhs, len(Y)))
+    for k in range(nrhs):
+        f = eval_ambient_modes(ambient_modes(seed + 7919 * k), Y)
+        F[k] = f / np.std(f)
+    return F
