@@ -408,6 +408,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Serving stream (no JSON bench line of the main metric): capacity of the seeded request
+    mix served back to back, then the same mix with Poisson arrivals at a fraction of that
+    capacity; p50/p99 latency (arrival to result), queue / service split; mixed (FP32
+    factors) against FP64 factors."""
+    import torch
+    from paper_1909_08734_gb300.serving import Request, Server, summarize
+    from workloads import (WORKLOADS, poisson_arrivals, serving_stream, smooth_rhs,
+                           surface_mesh)
+    V, T = surface_mesh(WORKLOADS["mesh_h001"])
+    specs = serving_stream(args.serving_requests, seed=5)
+    out = {"mode": "serving", "requests": len(specs), "stream_seed": 5,
+           "mix": "surface in {sphere, torus(1,0.4), 81,920-triangle mesh}, h in {0.05, 0.025, "
+                  "0.0125} w.p. {0.5, 0.35, 0.15}, c log-uniform [0.1, 100], 1-32 rhs, 25% "
+                  "backward-Euler chains, 30% operator reuse"}
+
+    def make_server(prec):
+        srv = Server(precision=prec)
+        srv.register_surface("sphere", "sphere", 1.0, 0.0)
+        srv.register_surface("torus", "torus", 1.0, 0.4)
+        srv.register_surface("mesh", "trimesh", verts=V, tris=T)
+        return srv
+
+    host = make_server("fp32")        # bands and right-hand sides, built once outside timing
+    rhs = {}
+    for sp in specs:
+        cp = host.band(sp.surface, sp.h)[2]
+        rhs[sp.rid] = smooth_rhs(cp, sp.rhs_seed, sp.nrhs)
+
+    def requests(arrivals):
+        return [Request(sp.rid, float(a), sp.surface, sp.h, sp.c, rhs[sp.rid], sp.chain_steps)
+                for sp, a in zip(specs, arrivals)]
+
+    for prec in args.serving_precisions.split(","):
+        srv = make_server(prec)
+        srv._bands = host._bands                  # share host-side bands and partitions
+        cap = summarize(srv.serve(requests(np.zeros(len(specs))), realtime=False))
+        srv.close()
+        res = {"capacity": cap}
+        for frac in [float(x) for x in args.serving_load.split(",")]:
+            rate = frac * cap["requests_per_s"]
+            srv = make_server(prec)
+            srv._bands = host._bands
+            st = summarize(srv.serve(requests(poisson_arrivals(len(specs), rate, seed=5))))
+            st["offered_rate_per_s"] = rate
+            st["counters"] = dict(srv.counters)
+            srv.close()
+            res[f"load_{frac:g}"] = st
+        out[prec] = res
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,11 +473,18 @@ def main():
     ap.add_argument("--kernel-only", type=int, default=0,
                     help="profiling aid: only N launches of the batched solve, no JSON bench line")
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--serving", action="store_true",
+                    help="serve the seeded request stream instead of the bench line")
+    ap.add_argument("--serving-requests", type=int, default=40)
+    ap.add_argument("--serving-load", default="0.7", help="offered load(s), fractions of capacity")
+    ap.add_argument("--serving-precisions", default="fp32,fp64")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.kernel_only:
         run_kernel_only(args)
+    elif args.serving:
+        run_serving(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

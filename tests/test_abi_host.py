@@ -129,3 +129,21 @@ def test_local_operators_match_oracle(pair, tr):
         Do = lp.A.toarray()
         # same sums of the same FP64 products, possibly in another order
         assert np.abs(D - Do).max() <= 8 * np.finfo(float).eps * np.abs(Do).max()
+
+
+def test_plan_is_host_only_and_consistent(pair):
+    """oras_plan needs no GPU; its factor bytes follow from the local sizes n_j of the local
+    operators (64-row tiles, 8/4/2 bytes per entry), and its bounds grow with the restart."""
+    band, part, OB, E, lab, ns, no = pair
+    sizes = [G.cpm_local_coo(band, part, 1.0, "oras", 4.0, 40.0, j)[0] for j in range(ns)]
+    tiles = sum(((n + 63) // 64) ** 2 for n in sizes) * 4096
+    plans = {p: G.oras_plan(band, part, "oras", p, 50, 1) for p in ("fp64", "fp32", "bf16")}
+    assert plans["fp64"]["factor_bytes"] == 8 * tiles
+    assert plans["fp32"]["factor_bytes"] == 4 * tiles
+    assert plans["bf16"]["factor_bytes"] == 2 * tiles
+    assert plans["fp32"]["sum_n2"] == sum(n * n for n in sizes)
+    for p in plans.values():
+        assert p["resident_bytes"] >= p["factor_bytes"] and p["setup_peak_bytes"] >= p["factor_bytes"]
+    assert G.oras_plan(band, part, "oras", "fp32", 80, 1)["resident_bytes"] > plans["fp32"]["resident_bytes"]
+    with pytest.raises(G.CpmError):
+        G.oras_plan(band, part, "oras", "fp32", 0, 1)
