@@ -344,6 +344,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   // FP32: split-tf32 tensor-core update (FP32 accuracy); BF16: bf16 inputs, FP32 accumulate
   const int use_tc = (precision == CPM_FP64 || simt_lu) ? 0 : (precision == CPM_BF16 ? 2 : 1);
   if (use_tc) CK(lu_tc_prepare());
+  CK(lu_panel_prepare());
   for (int step = 0; step < t_max; ++step) CK(launch_lu_step(f, step, use_tc, s));
   CK(launch_lu_finish(f, d_unk, d_unk_off, d_own, pc->gather, pc->scatter, dinv, s));
   void* inv;

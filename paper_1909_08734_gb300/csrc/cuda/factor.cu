@@ -9,8 +9,12 @@
 //            tensor-core version lives in lu_tc.cu)
 // FP64 mode keeps double tiles; FP32 and BF16 modes keep float tiles in the swizzled
 // layout of common.cuh.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace cpmdev {
 
@@ -120,6 +124,202 @@ __global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(T* a, const Sub
   }
 }
 
+// ---------------------------------------------------------------- panel in a cluster
+// The same panel factorisation with the panel held in shared memory: a cluster of CS CTAs
+// per subdomain, CTA r holding rows [k0 + r R, k0 + (r+1) R) of the panel's 64 columns.  Per
+// column: every CTA reduces its candidate (max |a|, lowest row on ties) -> cluster barrier ->
+// every CTA reads the CS candidates and the pivot row through distributed shared memory (the
+// pivot CTA also reads the row it swaps with) -> cluster barrier -> the two owners write the
+// swapped rows, every CTA updates its rows below the pivot and reduces the next column's
+// candidate in the same pass.  Same arithmetic, element by element, as lu_panel_kernel.
+constexpr int PC_THREADS = 256;
+constexpr int PC_STRIDE = 65;                 // panel row stride (elements)
+constexpr int PC_SMEM = 200 * 1024;           // dynamic shared memory for panel rows
+
+__device__ __forceinline__ void argmax_pair(double& v, int& i, double ov, int oi) {
+  if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+}
+
+// Block-wide (max value, lowest index) of the threads' pairs into *ov, *oi (thread 0 writes).
+__device__ __forceinline__ void block_argmax(double best, int bi, double* wv, int* wi, double* ov, int* oi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    argmax_pair(best, bi, __shfl_xor_sync(0xffffffffu, best, o), __shfl_xor_sync(0xffffffffu, bi, o));
+  if (lane == 0) { wv[warp] = best; wi[warp] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = wv[0];
+    int i = wi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmax_pair(b, i, wv[w], wi[w]);
+    *ov = b;
+    *oi = i;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PC_THREADS) lu_panel_cluster_kernel(T* a, const SubMeta* __restrict__ meta,
+                                                                      int32_t* ipiv, int* status, int s,
+                                                                      int rows_per_cta) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int cs = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const SubMeta m = meta[blockIdx.x / cs];
+  if (s >= m.T) return;                         // the whole cluster (one subdomain) leaves together
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* panel = (T*)smem_raw;
+  __shared__ double cval[2], wv[PC_THREADS / 32];
+  __shared__ int cidx[2], wi[PC_THREADS / 32];
+  __shared__ T prow[64], trow[64];
+  __shared__ int piv_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k0 = 64 * s, np = 64 * m.T;
+  const int r0 = k0 + rank * rows_per_cta;
+  const int nr = max(0, min(np, r0 + rows_per_cta) - r0);
+  for (int e = tid; e < nr * 64; e += PC_THREADS) {
+    const int i = e % nr, j = e / nr;
+    panel[i * PC_STRIDE + j] = at(a, m, r0 + i, k0 + j);
+  }
+  __syncthreads();
+  {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < nr; i += PC_THREADS) {
+      const double v = fabs((double)panel[i * PC_STRIDE]);
+      if (v > best) { best = v; bi = r0 + i; }
+    }
+    block_argmax(best, bi, wv, wi, &cval[0], &cidx[0]);
+  }
+  for (int c = 0; c < 64; ++c) {
+    const int col = k0 + c, slot = c & 1;
+    cl.sync();                                  // candidates of column c are visible
+    if (warp == 0) {
+      double v = -1.0;
+      int ix = 0x7fffffff;
+      if (lane < cs) {
+        v = *cl.map_shared_rank(&cval[slot], lane);
+        ix = *cl.map_shared_rank(&cidx[slot], lane);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        argmax_pair(v, ix, __shfl_xor_sync(0xffffffffu, v, o), __shfl_xor_sync(0xffffffffu, ix, o));
+      if (lane == 0) {
+        if (!(v > 0.0)) {                       // zero (or NaN) column: singular local matrix
+          if (rank == 0) atomicOr(status, ST_SINGULAR);
+          ix = col;
+        }
+        piv_sh = ix;
+      }
+    }
+    __syncthreads();
+    const int p = piv_sh;
+    const int oc = (col - k0) / rows_per_cta, op = (p - k0) / rows_per_cta;
+    if (tid < 64) {
+      prow[tid] = cl.map_shared_rank(panel, op)[(p - (k0 + op * rows_per_cta)) * PC_STRIDE + tid];
+      if (rank == op && p != col)
+        trow[tid] = cl.map_shared_rank(panel, oc)[(col - (k0 + oc * rows_per_cta)) * PC_STRIDE + tid];
+    }
+    cl.sync();                                  // rows col and p have been read everywhere
+    if (p != col && tid < 64) {
+      if (rank == oc) panel[(col - r0) * PC_STRIDE + tid] = prow[tid];
+      if (rank == op) panel[(p - r0) * PC_STRIDE + tid] = trow[tid];
+    }
+    if (rank == 0 && tid == 0) ipiv[m.row_off + col] = p;
+    __syncthreads();
+    const T d = prow[c];
+    const T inv = d != (T)0 ? (T)1 / d : (T)0;
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = max(0, col + 1 - r0) + tid; i < nr; i += PC_THREADS) {
+      T* row = panel + i * PC_STRIDE;
+      const T l = row[c] * inv;
+      row[c] = l;
+      for (int cc = c + 1; cc < 64; ++cc) row[cc] -= l * prow[cc];
+      if (c + 1 < 64) {
+        const double v = fabs((double)row[c + 1]);
+        if (v > best) { best = v; bi = r0 + i; }
+      }
+    }
+    if (c + 1 < 64) block_argmax(best, bi, wv, wi, &cval[slot ^ 1], &cidx[slot ^ 1]);
+  }
+  __syncthreads();
+  for (int e = tid; e < nr * 64; e += PC_THREADS) {
+    const int i = e % nr, j = e / nr;
+    at(a, m, r0 + i, k0 + j) = panel[i * PC_STRIDE + j];
+  }
+  cl.sync();                                    // no CTA leaves while its panel may be read
+}
+
+// Cluster size and rows per CTA for a panel of at most max_rows rows; 0 if it does not fit.
+static int panel_cluster_size(int max_rows, size_t elem, int* rows_per_cta) {
+  const int cap = PC_SMEM / (PC_STRIDE * (int)elem);
+  for (int cs = 1; cs <= 16; cs *= 2) {
+    const int r = (max_rows + cs - 1) / cs;
+    if (r <= cap) {
+      *rows_per_cta = r;
+      return cs;
+    }
+  }
+  return 0;
+}
+
+template <typename T>
+static cudaError_t launch_panel_cluster(const FactorDev& f, int step, int cs, int rpc, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(f.n_sub * cs);
+  cfg.blockDim = dim3(PC_THREADS);
+  cfg.dynamicSmemBytes = (size_t)rpc * PC_STRIDE * sizeof(T);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T>, (T*)f.a, f.meta, f.ipiv, f.status, step, rpc);
+}
+
+// Largest cluster size the device can co-schedule with the panel kernel's shared memory.
+static int g_panel_max_cs[2] = {0, 0};
+
+cudaError_t lu_panel_prepare() {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(lu_panel_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, PC_SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lu_panel_cluster_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, PC_SMEM);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lu_panel_cluster_kernel<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(lu_panel_cluster_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  for (int k = 0; k < 2; ++k) {
+    g_panel_max_cs[k] = 0;
+    for (int cs = 16; cs >= 1 && !g_panel_max_cs[k]; cs /= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(cs);
+      cfg.blockDim = dim3(PC_THREADS);
+      cfg.dynamicSmemBytes = PC_SMEM;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = cs;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      e = k ? cudaOccupancyMaxActiveClusters(&n, lu_panel_cluster_kernel<double>, &cfg)
+            : cudaOccupancyMaxActiveClusters(&n, lu_panel_cluster_kernel<float>, &cfg);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+      }
+      if (n > 0) g_panel_max_cs[k] = cs;
+    }
+  }
+  return cudaSuccess;
+}
+
 // ---------------------------------------------------------------- row interchanges
 template <typename T>
 __global__ void lu_swap_kernel(T* a, const SubMeta* __restrict__ meta, const int32_t* __restrict__ ipiv,
@@ -215,9 +415,17 @@ __global__ void __launch_bounds__(256) lu_update_simt_kernel(T* a, const SubMeta
 
 cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_t s) {
   const int W = f.t_max - 1 - step;
+  int rpc = 0;
+  const int cs = panel_cluster_size(64 * (f.t_max - step), f.fp64 ? 8 : 4, &rpc);
+  const bool cluster = cs > 0 && cs <= g_panel_max_cs[f.fp64 ? 1 : 0];
   if (f.fp64) {
     double* a = (double*)f.a;
-    lu_panel_kernel<double><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+    if (cluster) {
+      cudaError_t e = launch_panel_cluster<double>(f, step, cs, rpc, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      lu_panel_kernel<double><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+    }
     lu_swap_kernel<double><<<dim3(f.t_max, f.n_sub), 64, 0, s>>>(a, f.meta, f.ipiv, step);
     if (W > 0) {
       lu_trsm_kernel<double><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step);
@@ -227,7 +435,12 @@ cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_
     }
   } else {
     float* a = (float*)f.a;
-    lu_panel_kernel<float><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+    if (cluster) {
+      cudaError_t e = launch_panel_cluster<float>(f, step, cs, rpc, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      lu_panel_kernel<float><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+    }
     lu_swap_kernel<float><<<dim3(f.t_max, f.n_sub), 64, 0, s>>>(a, f.meta, f.ipiv, step);
     if (W > 0) {
       lu_trsm_kernel<float><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step);

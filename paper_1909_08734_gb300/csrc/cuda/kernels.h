@@ -71,6 +71,9 @@ cudaError_t launch_pad_identity(void* a, int fp64, const SubMeta* meta, int n_su
 cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_t s);
 cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s);
 cudaError_t lu_tc_prepare();
+// Panel factorisation in a thread-block cluster (shared-memory panel); call once per device
+// before launch_lu_step.  Without it the panel runs on one CTA per subdomain from global memory.
+cudaError_t lu_panel_prepare();
 cudaError_t launch_lu_finish(const FactorDev& f, const int32_t* unknowns, const int64_t* unk_off,
                              const int32_t* own_flag, int32_t* gather, int32_t* scatter,
                              void* dinv, cudaStream_t s);
