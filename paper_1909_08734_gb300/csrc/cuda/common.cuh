@@ -101,13 +101,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for a phase of an mbarrier; returns false after the limit.
+// Device time in ns (the global timer).
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Time limit of a wait on this CTA's own copies or tensor-core work, far above any
+// legitimate wait; then the kernel reports CPM_ERR_TIMEOUT instead of hanging.
+constexpr uint64_t MBAR_WAIT_LIMIT_NS = 2000000000ull;
+// Bounded wait for a phase of an mbarrier; returns false after the time limit.  try_wait
+// suspends the thread in hardware until the phase completes or a short window passes, so
+// the loop polls without sleeping (a sleep would add its granularity to every wait).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < SPIN_LIMIT; ++it) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (it > 64) __nanosleep(256);
+    if ((it & 31) == 0 && global_ns() - t0 > MBAR_WAIT_LIMIT_NS) return false;
   }
-  return false;
 }
 
 // ---- reductions -----------------------------------------------------------------------

@@ -69,7 +69,8 @@ cudaError_t launch_pad_identity(void* a, int fp64, const SubMeta* meta, int n_su
                                 cudaStream_t s);
 // use_tc: 0 SIMT update, 1 tensor cores with split-tf32 operands, 2 tensor cores with bf16
 cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_t s);
-cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s);
+// jchunk: tile columns per CTA (0 = default)
+cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s, int jchunk = 0);
 cudaError_t lu_tc_prepare();
 // Panel factorisation in a thread-block cluster (shared-memory panel); call once per device
 // before launch_lu_step.  Without it the panel runs on one CTA per subdomain from global memory.

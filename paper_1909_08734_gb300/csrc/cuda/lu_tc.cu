@@ -2,7 +2,7 @@
 //     A_IJ -= L_Is U_sJ        for all I, J > s and all subdomains, in one launch.
 //
 // One CTA (4 warps) computes 128 x 64 blocks: tile rows I0 = s+1+2p and I0+1 of a chunk of
-// tile columns J.  The FP32 tile storage (1 KB atoms of 32 rows x 8 columns, 128-byte XOR
+// tile columns J, with the U tiles and the C tiles double-buffered in shared memory.  The FP32 tile storage (1 KB atoms of 32 rows x 8 columns, 128-byte XOR
 // swizzle, row index contiguous) is the canonical K-major tcgen05 layout for a B operand
 // (rows = K, columns = N): U tiles are used as loaded by one 16 KB bulk copy.  The L tiles
 // are the A operand (rows = M, columns = K); they are rewritten K-major while they are
@@ -12,8 +12,9 @@
 //              keeps FP32 accuracy.
 //   BF16 mode: operands are rounded to bf16 into bf16 canonical layouts (kind::f16, FP32
 //              accumulation).
-// D (128 lanes x 64 FP32 columns) lives in tensor memory; the epilogue reads it with
-// tcgen05.ld (warp w owns rows 32w..32w+31) and subtracts it from the FP32 tiles.
+// D (128 lanes x 64 FP32 columns, two buffers) lives in tensor memory; the epilogue reads it
+// with tcgen05.ld (warp w owns rows 32 (w & 3) + lane and half of the columns) and subtracts
+// it from the FP32 tiles while the next column's MMAs run.
 // Every wait is bounded; on expiry the CTA reports CPM_ERR_TIMEOUT, still frees its tensor
 // memory, and returns.
 #include "common.cuh"
@@ -21,7 +22,8 @@
 
 namespace cpmdev {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;          // 8 warps: two per tensor-memory lane quarter
+constexpr int TC_TMEM_COLS = 64;         // FP32 accumulator columns per buffer (two buffers)
 
 // ---- tcgen05 / descriptor helpers -------------------------------------------------------
 // Shared-memory matrix descriptor (tcgen05): start address, leading / stride byte offsets,
@@ -126,61 +128,77 @@ __device__ __forceinline__ uint32_t bf16_b_off(int k, int n) {
 }
 
 // KIND 2: FP32 tiles, split tf32.  KIND 1: FP32 tiles, bf16 operands.
-// Grid: x = pair of tile rows (I0 = s+1+2x, I0+1), y = chunk of JCHUNK tile columns,
-// z = subdomain.  The A pair is loaded and converted once; B tiles of the chunk stream
-// through two stages (bulk copies two ahead); each thread loads its C row before the
-// tensor cores finish, then subtracts the accumulator read from tensor memory.
-constexpr int JCHUNK = 8;
+// Grid: x = pair of tile rows (I0 = s+1+2x, I0+1), y = chunk of jchunk tile columns,
+// z = subdomain.  The A pair is loaded and converted once.  The U tiles (B) and the C tile
+// pairs of the chunk stream through two shared-memory stages each, by bulk copies issued
+// two columns ahead, so that HBM traffic overlaps the conversion, the MMAs and the epilogue
+// (C = C - D with D read from tensor memory, written straight back to the tiles).
+constexpr int TC_JCHUNK = 32;           // tile columns per CTA (default of launch_lu_update_tc)
 template <int KIND> struct TcSmem;
-template <> struct TcSmem<2> {    // tf32 split: A raw 32 KB, A hi/lo 64 KB, B stages 2 x (hi 16 + lo 16 KB)
-  static constexpr uint32_t A_RAW = 0, A_HI = 32768, A_LO = 65536, B0 = 98304, BSTAGE = 32768,
-                            TOTAL = 163840;
+template <> struct TcSmem<2> {    // A hi / lo 64 KB, B stages 2 x (hi 16 + lo 16 KB), C stages 2 x 32 KB
+  static constexpr uint32_t A_HI = 0, A_LO = 32768, B0 = 65536, BSTAGE = 32768, C0 = 131072, CSTAGE = 32768,
+                            A_RAW = C0 + CSTAGE, TOTAL = 196608;
 };
-template <> struct TcSmem<1> {    // bf16: A raw 32 KB + A bf16 16 KB, B stages 2 x (raw 16 KB + bf16 8 KB)
-  static constexpr uint32_t A_RAW = 0, A_BF = 32768, B0 = 49152, BSTAGE = 24576, TOTAL = 98304;
+template <> struct TcSmem<1> {    // A bf16 16 KB, B stages 2 x (raw 16 + bf16 8 KB), C stages 2 x 32 KB
+  static constexpr uint32_t A_BF = 0, B0 = 16384, BSTAGE = 24576, C0 = 65536, CSTAGE = 32768,
+                            A_RAW = C0 + CSTAGE, TOTAL = 131072;
 };
+// (the raw A pair is staged in C stage 1, which is refilled once A has been converted)
 
 template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, const SubMeta* __restrict__ meta,
-                                                                   int s, int* status) {
+                                                                   int s, int jchunk, int* status) {
   using L = TcSmem<KIND>;
   const SubMeta m = meta[blockIdx.z];
   const int I0 = s + 1 + 2 * blockIdx.x, I1 = I0 + 1;
-  const int Jbeg = s + 1 + blockIdx.y * JCHUNK;
+  const int Jbeg = s + 1 + blockIdx.y * jchunk;
   if (I0 >= m.T || Jbeg >= m.T) return;        // before any tensor-memory allocation
-  const int Jend = min(m.T, Jbeg + JCHUNK);
+  const int nJ = min(m.T, Jbeg + jchunk) - Jbeg;
   const bool two = I1 < m.T;
+  const uint32_t pair_bytes = two ? 32768u : 16384u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bar_a, bar_b[2], bar_mma;
+  __shared__ __align__(8) uint64_t bar_a, bar_b[2], bar_c[2], bar_mma[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int sh_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  int nissued[2] = {0, 0}, nwaited[2] = {0, 0};   // bulk copies per B stage (thread 0)
-  bool a_done = false, mma_pending = false;
+  // copies and commits issued / waited per stage (thread 0), for the drain after an abort
+  int nb_iss[2] = {0, 0}, nb_wait[2] = {0, 0}, nc_iss[2] = {0, 0}, nc_wait[2] = {0, 0};
+  int nm_iss[2] = {0, 0}, nm_wait[2] = {0, 0};
+  bool a_done = false;
   if (tid == 0) {
     mbar_init(&bar_a, 1);
-    mbar_init(&bar_b[0], 1);
-    mbar_init(&bar_b[1], 1);
-    mbar_init(&bar_mma, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_b[b], 1);
+      mbar_init(&bar_c[b], 1);
+      mbar_init(&bar_mma[b], 1);
+    }
     fence_mbar_init();
   }
-  if (warp == 0) tmem_alloc(&tmem_slot, 64);
+  if (warp == 0) tmem_alloc(&tmem_slot, 2 * TC_TMEM_COLS);
   __syncthreads();
   fence_after_sync();
   const uint32_t taddr = tmem_slot;
-  // raw FP32 destinations of the A pair and of the B stages
   float* rawA = (float*)(base + L::A_RAW);
-  auto rawB = [&](int b) { return (float*)(base + L::B0 + b * L::BSTAGE); };
+  auto stage_b = [&](int b) { return (float*)(base + L::B0 + b * L::BSTAGE); };
+  auto stage_c = [&](int b) { return (float*)(base + L::C0 + b * L::CSTAGE); };
+  auto issue_b = [&](int b, int J) {
+    mbar_expect_tx(&bar_b[b], 16384u);
+    bulk_g2s(stage_b(b), a + tile_base(m, s, J), 16384, &bar_b[b]);
+    nb_iss[b]++;
+  };
+  auto issue_c = [&](int b, int J) {
+    mbar_expect_tx(&bar_c[b], pair_bytes);
+    bulk_g2s(stage_c(b), a + tile_base(m, I0, J), 16384, &bar_c[b]);
+    if (two) bulk_g2s(stage_c(b) + TILE_ELEMS, a + tile_base(m, I1, J), 16384, &bar_c[b]);
+    nc_iss[b]++;
+  };
   if (tid == 0) {
-    mbar_expect_tx(&bar_a, two ? 32768u : 16384u);
+    mbar_expect_tx(&bar_a, pair_bytes);
     bulk_g2s(rawA, a + tile_base(m, I0, s), 16384, &bar_a);
     if (two) bulk_g2s(rawA + TILE_ELEMS, a + tile_base(m, I1, s), 16384, &bar_a);
-    for (int b = 0; b < 2 && Jbeg + b < Jend; ++b) {
-      mbar_expect_tx(&bar_b[b], 16384u);
-      bulk_g2s(rawB(b), a + tile_base(m, s, Jbeg + b), 16384, &bar_b[b]);
-      nissued[b]++;
-    }
+    for (int b = 0; b < 2 && b < nJ; ++b) issue_b(b, Jbeg + b);
+    issue_c(0, Jbeg);
     sh_ok = mbar_wait_bounded(&bar_a, 0) ? 1 : 0;
     if (!sh_ok) atomicOr(status, ST_TIMEOUT);
     a_done = sh_ok;
@@ -210,107 +228,139 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
             __float2bfloat16_rn(rawA[t * TILE_ELEMS + off_sw32(i, k)]);
       }
     }
+    fence_proxy_async();                        // generic accesses before the async refill
+    __syncthreads();                            // raw A consumed: C stage 1 is free
+    if (tid == 0 && nJ > 1) issue_c(1, Jbeg + 1);
   }
-  const int row = 32 * warp + lane;
+  // epilogue assignment: warp w owns rows 32 (w & 3) + lane (tensor-memory lanes of its
+  // quarter) and columns 32 (w >> 2) .. + 31
+  const int row = 32 * (warp & 3) + lane, colh = warp >> 2;
   const bool mine = row < 64 || two;
   const int lr = row & 63;
-  for (int it = 0; ok && it < Jend - Jbeg; ++it) {
-    const int J = Jbeg + it, b = it & 1;
-    const uint32_t ph = (uint32_t)(it >> 1) & 1;
-    float* ct = a + tile_base(m, row < 64 ? I0 : I1, J);
-    float c[64];
-    if (mine) {
+  int v_line[8];                                // in-atom offset of column line l of this row
 #pragma unroll
-      for (int q = 0; q < 64; ++q) c[q] = ct[off_sw32(lr, q)];
-    }
-    if (tid == 0) {
-      sh_ok = mbar_wait_bounded(&bar_b[b], ph) ? 1 : 0;
-      if (!sh_ok) atomicOr(status, ST_TIMEOUT);
-      else nwaited[b]++;
-    }
-    __syncthreads();
-    if (!sh_ok) { ok = false; break; }
-    mbar_wait_bounded(&bar_b[b], ph);
-    float* rb = rawB(b);
-    if (KIND == 2) {                            // B_hi in place, B_lo in the second half
-      float* blo = rb + TILE_ELEMS;
-      for (int e = tid; e < TILE_ELEMS; e += TC_THREADS) {
-        const float x = rb[e], hi = tf32_round(x);
-        rb[e] = hi;
-        blo[e] = tf32_round(x - hi);
+  for (int l = 0; l < 8; ++l) v_line[l] = (l << 5) + ((((lr >> 2) & 7) ^ l) << 2);
+  // software pipeline: iteration it converts U tile J = Jbeg + it and issues its MMAs into
+  // accumulator buffer it & 1, then finishes column J - 1 (epilogue from buffer (it-1) & 1)
+  for (int it = 0; ok && it <= nJ; ++it) {
+    if (it < nJ) {
+      const int b = it & 1;
+      const uint32_t ph = (uint32_t)(it >> 1) & 1;
+      if (tid == 0) {
+        sh_ok = mbar_wait_bounded(&bar_b[b], ph) ? 1 : 0;
+        if (!sh_ok) atomicOr(status, ST_TIMEOUT);
+        else nb_wait[b]++;
       }
-    } else {
-      unsigned char* bbf = (unsigned char*)(rb + TILE_ELEMS);
-      for (int e = tid; e < TILE_ELEMS; e += TC_THREADS) {
-        const int k = e & 63, n = e >> 6;
-        *(__nv_bfloat16*)(bbf + bf16_b_off(k, n)) = __float2bfloat16_rn(rb[off_sw32(k, n)]);
-      }
-    }
-    fence_proxy_async();                        // generic-proxy writes -> tensor-core reads
-    __syncthreads();
-    if (tid == 0) {
-      fence_after_sync();
-      const uint32_t sb = smem_u32(base), bs = smem_u32(rb);
-      if (KIND == 2) {
-        constexpr uint32_t idesc = instr_desc(2);
-        const uint32_t ahi = sb + TcSmem<2>::A_HI, alo = sb + TcSmem<2>::A_LO;
-        const uint32_t bhi = bs, blo = bs + 16384;
-        for (int k = 0; k < 8; ++k) {           // K = 8 tf32 values (32 bytes) per instruction
-          const uint32_t ka = (k >> 2) * 16384 + (k & 3) * 32;
-          const uint32_t kb = (k >> 2) * 8192 + (k & 3) * 32;
-          mma<2>(taddr, smem_desc(ahi + ka, 16, 1024), smem_desc(bhi + kb, 16, 1024), idesc,
-                 k > 0 ? 1u : 0u);
-          mma<2>(taddr, smem_desc(ahi + ka, 16, 1024), smem_desc(blo + kb, 16, 1024), idesc, 1u);
-          mma<2>(taddr, smem_desc(alo + ka, 16, 1024), smem_desc(bhi + kb, 16, 1024), idesc, 1u);
+      __syncthreads();
+      if (!sh_ok) { ok = false; break; }
+      mbar_wait_bounded(&bar_b[b], ph);
+      float* rb = stage_b(b);
+      if (KIND == 2) {                          // B_hi in place, B_lo in the second half
+        float4* b4 = (float4*)rb;
+        float4* l4 = (float4*)(rb + TILE_ELEMS);
+#pragma unroll
+        for (int e = tid; e < TILE_ELEMS / 4; e += TC_THREADS) {
+          const float4 x = b4[e];
+          float4 hi, lo;
+          hi.x = tf32_round(x.x); lo.x = tf32_round(x.x - hi.x);
+          hi.y = tf32_round(x.y); lo.y = tf32_round(x.y - hi.y);
+          hi.z = tf32_round(x.z); lo.z = tf32_round(x.z - hi.z);
+          hi.w = tf32_round(x.w); lo.w = tf32_round(x.w - hi.w);
+          b4[e] = hi;
+          l4[e] = lo;
         }
       } else {
-        constexpr uint32_t idesc = instr_desc(1);
-        const uint32_t ab = sb + TcSmem<1>::A_BF, bb = bs + 16384;
-        for (int k = 0; k < 4; ++k)             // K = 16 bf16 values (32 bytes) per instruction
-          mma<1>(taddr, smem_desc(ab + k * 32, 16, 1024), smem_desc(bb + k * 32, 16, 1024), idesc,
-                 k > 0 ? 1u : 0u);
+        unsigned char* bbf = (unsigned char*)(rb + TILE_ELEMS);
+        for (int e = tid; e < TILE_ELEMS; e += TC_THREADS) {
+          const int k = e & 63, n = e >> 6;
+          *(__nv_bfloat16*)(bbf + bf16_b_off(k, n)) = __float2bfloat16_rn(rb[off_sw32(k, n)]);
+        }
       }
-      mma_commit(&bar_mma);
-      sh_ok = mbar_wait_bounded(&bar_mma, (uint32_t)it & 1) ? 1 : 0;
-      if (!sh_ok) {
-        atomicOr(status, ST_TIMEOUT);
-        mma_pending = true;
-      }
-      // stage b is free again: stream the tile two columns ahead into it
-      if (sh_ok && J + 2 < Jend) {
-        mbar_expect_tx(&bar_b[b], 16384u);
-        bulk_g2s(rb, a + tile_base(m, s, J + 2), 16384, &bar_b[b]);
-        nissued[b]++;
+      fence_proxy_async();                      // generic-proxy writes -> tensor-core reads
+      __syncthreads();
+      if (tid == 0) {
+        fence_after_sync();
+        const uint32_t d_tmem = taddr + (uint32_t)(b * TC_TMEM_COLS);
+        // a descriptor's start-address field holds addr >> 4: an offset adds (off >> 4)
+        const uint64_t db = smem_desc(smem_u32(rb), 16, 1024);
+        if (KIND == 2) {
+          constexpr uint32_t idesc = instr_desc(2);
+          const uint64_t dhi = smem_desc(smem_u32(base) + TcSmem<2>::A_HI, 16, 1024);
+          const uint64_t dlo = smem_desc(smem_u32(base) + TcSmem<2>::A_LO, 16, 1024);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {         // K = 8 tf32 values (32 bytes) per instruction
+            const uint64_t ka = ((k >> 2) * 16384 + (k & 3) * 32) >> 4;
+            const uint64_t kb = ((k >> 2) * 8192 + (k & 3) * 32) >> 4;
+            mma<2>(d_tmem, dhi + ka, db + kb, idesc, k > 0 ? 1u : 0u);
+            mma<2>(d_tmem, dhi + ka, db + (16384 >> 4) + kb, idesc, 1u);
+            mma<2>(d_tmem, dlo + ka, db + kb, idesc, 1u);
+          }
+        } else {
+          constexpr uint32_t idesc = instr_desc(1);
+          const uint64_t da = smem_desc(smem_u32(base) + TcSmem<1>::A_BF, 16, 1024);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)           // K = 16 bf16 values (32 bytes) per instruction
+            mma<1>(d_tmem, da + ((k * 32) >> 4), db + ((16384 + k * 32) >> 4), idesc, k > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar_mma[b]);
+        nm_iss[b]++;
       }
     }
-    __syncthreads();
-    if (!sh_ok) { ok = false; break; }
-    mbar_wait_bounded(&bar_mma, (uint32_t)it & 1);
-    fence_after_sync();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    if (it > 0) {                               // finish column J - 1
+      const int p = it - 1, bp = p & 1;
+      const uint32_t php = (uint32_t)(p >> 1) & 1;
+      if (tid == 0) {
+        sh_ok = mbar_wait_bounded(&bar_mma[bp], php) ? 1 : 0;
+        if (!sh_ok) atomicOr(status, ST_TIMEOUT);
+        else nm_wait[bp]++;
+        // U stage bp is free again: stream the tile two columns ahead into it
+        if (sh_ok && p + 2 < nJ) {
+          fence_proxy_async();
+          issue_b(bp, Jbeg + p + 2);
+        }
+        if (sh_ok) {
+          sh_ok = mbar_wait_bounded(&bar_c[bp], php) ? 1 : 0;
+          if (!sh_ok) atomicOr(status, ST_TIMEOUT);
+          else nc_wait[bp]++;
+        }
+      }
+      __syncthreads();
+      if (!sh_ok) { ok = false; break; }
+      mbar_wait_bounded(&bar_mma[bp], php);
+      mbar_wait_bounded(&bar_c[bp], php);
+      fence_after_sync();
+      // element (lr, 32 colh + q) of a tile sits at row_base + (q >> 3) * 256 + v[q & 7]
+      const int row_base = ((lr >> 5) * 8 + 4 * colh) * 256 + (lr & 3);
+      const float* cs = stage_c(bp) + (row < 64 ? 0 : TILE_ELEMS) + row_base;
+      float* ct = a + tile_base(m, row < 64 ? I0 : I1, Jbeg + p) + row_base;
       float d[32];
-      tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + 32 * h, d);
+      tmem_ld32(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bp * TC_TMEM_COLS + 32 * colh), d);
       if (mine) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) ct[off_sw32(lr, 32 * h + q)] = c[32 * h + q] - d[q];
+        for (int q = 0; q < 32; ++q) {
+          const int o = (q >> 3) * 256 + v_line[q & 7];
+          ct[o] = cs[o] - d[q];
+        }
       }
+      fence_before_sync();
+      fence_proxy_async();
+      __syncthreads();                          // accumulator buffer and C stage read
+      if (tid == 0 && p + 2 < nJ) issue_c(bp, Jbeg + p + 2);
     }
-    fence_before_sync();
-    __syncthreads();                            // accumulator read before the next MMA
   }
   // after an abort: wait (bounded) for this CTA's own copies and tensor-core work still in
   // flight before the shared and tensor memory are released
   if (tid == 0 && !ok) {
     if (!a_done) mbar_wait_bounded(&bar_a, 0);
-    for (int b = 0; b < 2; ++b)
-      for (; nwaited[b] < nissued[b]; ++nwaited[b]) mbar_wait_bounded(&bar_b[b], (uint32_t)nwaited[b] & 1);
-    if (mma_pending) mbar_wait_bounded(&bar_mma, 0);
-    if (mma_pending) mbar_wait_bounded(&bar_mma, 1);
+    for (int b = 0; b < 2; ++b) {
+      for (; nb_wait[b] < nb_iss[b]; ++nb_wait[b]) mbar_wait_bounded(&bar_b[b], (uint32_t)nb_wait[b] & 1);
+      for (; nc_wait[b] < nc_iss[b]; ++nc_wait[b]) mbar_wait_bounded(&bar_c[b], (uint32_t)nc_wait[b] & 1);
+      for (; nm_wait[b] < nm_iss[b]; ++nm_wait[b]) mbar_wait_bounded(&bar_mma[b], (uint32_t)nm_wait[b] & 1);
+    }
   }
   fence_before_sync();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(taddr, 64);
+  if (warp == 0) tmem_dealloc(taddr, 2 * TC_TMEM_COLS);
 }
 
 cudaError_t lu_tc_prepare() {
@@ -321,14 +371,15 @@ cudaError_t lu_tc_prepare() {
                               (int)(1024 + TcSmem<1>::TOTAL));
 }
 
-cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s) {
+cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s, int jchunk) {
   const int W = f.t_max - 1 - step;
   if (W <= 0) return cudaSuccess;
-  dim3 g((W + 1) / 2, (W + JCHUNK - 1) / JCHUNK, f.n_sub);
+  if (jchunk < 1) jchunk = TC_JCHUNK;
+  dim3 g((W + 1) / 2, (W + jchunk - 1) / jchunk, f.n_sub);
   if (bf16)
-    lu_update_tc_kernel<1><<<g, TC_THREADS, 1024 + TcSmem<1>::TOTAL, s>>>((float*)f.a, f.meta, step, f.status);
+    lu_update_tc_kernel<1><<<g, TC_THREADS, 1024 + TcSmem<1>::TOTAL, s>>>((float*)f.a, f.meta, step, jchunk, f.status);
   else
-    lu_update_tc_kernel<2><<<g, TC_THREADS, 1024 + TcSmem<2>::TOTAL, s>>>((float*)f.a, f.meta, step, f.status);
+    lu_update_tc_kernel<2><<<g, TC_THREADS, 1024 + TcSmem<2>::TOTAL, s>>>((float*)f.a, f.meta, step, jchunk, f.status);
   return cudaGetLastError();
 }
 
