@@ -49,31 +49,37 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
 
 // Tagged publication of one value.
 template <typename C> struct Tagged;
+// load() issues the word loads (their latency can overlap other work); check() accepts them
+// if they carry the expected tag.
 template <> struct Tagged<float> {
   static constexpr int WORDS = 1;
+  struct Raw { uint64_t w; };
   __device__ static void put(uint64_t* p, float v, uint32_t tag) {
     st_relaxed_u64(p, ((uint64_t)tag << 32) | (uint64_t)__float_as_uint(v));
   }
-  __device__ static bool get(const uint64_t* p, uint32_t tag, float* v) {
-    const uint64_t w = ld_relaxed_u64(p);
-    if ((uint32_t)(w >> 32) != tag) return false;
-    *v = __uint_as_float((uint32_t)w);
+  __device__ static Raw load(const uint64_t* p) { return Raw{ld_relaxed_u64(p)}; }
+  __device__ static bool check(const Raw& r, uint32_t tag, float* v) {
+    if ((uint32_t)(r.w >> 32) != tag) return false;
+    *v = __uint_as_float((uint32_t)r.w);
     return true;
   }
+  __device__ static bool get(const uint64_t* p, uint32_t tag, float* v) { return check(load(p), tag, v); }
 };
 template <> struct Tagged<double> {
   static constexpr int WORDS = 2;
+  struct Raw { uint64_t hi, lo; };
   __device__ static void put(uint64_t* p, double v, uint32_t tag) {
     const uint64_t b = (uint64_t)__double_as_longlong(v);
     st_relaxed_u64(p, ((uint64_t)tag << 32) | (b >> 32));
     st_relaxed_u64(p + 1, ((uint64_t)tag << 32) | (b & 0xffffffffull));
   }
-  __device__ static bool get(const uint64_t* p, uint32_t tag, double* v) {
-    const uint64_t hi = ld_relaxed_u64(p), lo = ld_relaxed_u64(p + 1);
-    if ((uint32_t)(hi >> 32) != tag || (uint32_t)(lo >> 32) != tag) return false;
-    *v = __longlong_as_double((long long)(((hi & 0xffffffffull) << 32) | (lo & 0xffffffffull)));
+  __device__ static Raw load(const uint64_t* p) { return Raw{ld_relaxed_u64(p), ld_relaxed_u64(p + 1)}; }
+  __device__ static bool check(const Raw& r, uint32_t tag, double* v) {
+    if ((uint32_t)(r.hi >> 32) != tag || (uint32_t)(r.lo >> 32) != tag) return false;
+    *v = __longlong_as_double((long long)(((r.hi & 0xffffffffull) << 32) | (r.lo & 0xffffffffull)));
     return true;
   }
+  __device__ static bool get(const uint64_t* p, uint32_t tag, double* v) { return check(load(p), tag, v); }
 };
 
 // Poll one tagged value until it carries tag; false on abort or after the spin limit.
@@ -130,8 +136,9 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   constexpr int CPS = STAGE / sizeof(C);                      // C values per stage
   static_assert(PIECES >= 1 && PIECES <= 2 && NSTAGE >= PIECES, "ring too small");
   __shared__ __align__(8) uint64_t bar[NSTAGE];
-  __shared__ C yb[64];
-  __shared__ C red[TRSV_THREADS];
+  __shared__ C yb[2][64];                                     // solved pieces, double-buffered
+  __shared__ C xb[64];
+  __shared__ C red[TRSV_THREADS], red2[TRSV_THREADS];
   __shared__ int sh_cur, sh_mb;
   const int tid = threadIdx.x;
   const S* tiles = (const S*)t.tiles;
@@ -201,17 +208,12 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   }
   __syncthreads();
 
-  // thread 0 waits (bounded) for stage c; then every thread observes the phase
-  auto wait_stage = [&](uint32_t c) -> bool {
-    if (tid == 0) {
-      const bool ok = mbar_wait_bounded(&bar[c % NSTAGE], (c / NSTAGE) & 1);
-      if (!ok) { atomicOr(t.status, ST_TIMEOUT); atomicExch(&t.sync[3], 1u); }
-      sh_mb = ok ? 0 : 1;
-    }
-    __syncthreads();
-    if (sh_mb) return false;
-    mbar_wait_bounded(&bar[c % NSTAGE], (c / NSTAGE) & 1);   // already complete
-    return true;
+  // every thread waits (bounded) for stage c itself; a failed wait raises the abort word and
+  // is folded into the next block-wide vote
+  auto stage_ready = [&](uint32_t c) -> bool {
+    const bool ok = mbar_wait_bounded(&bar[c % NSTAGE], (c / NSTAGE) & 1);
+    if (!ok) { atomicOr(t.status, ST_TIMEOUT); atomicExch(&t.sync[3], 1u); }
+    return ok;
   };
 
   while (!bad) {
@@ -228,10 +230,18 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
       const int g = t.gather[ro + tid];
       if (g >= 0) rhs = (C)rin[g];
     }
+    // tagged words of the solved piece multiplying off-diagonal tile l of this item
+    auto ywords = [&](int l) {
+      const int q = e.q0 + l;
+      const int J = e.bwd ? e.T - 1 - q : q;
+      return t.ytag + (m.row_off + 64 * J + tid) * W;
+    };
+    typename Tagged<C>::Raw pre{};
+    if (tid < 64 && e.nq > 0) pre = Tagged<C>::load(ywords(0));
     C acc = (C)0, psum = (C)0;
     for (int l = 0; l < e.nq; ++l) {
-      if (!wait_stage(cc)) { bad = true; break; }
-      bool ok = true;
+      const bool staged = stage_ready(cc);
+      bool ok = staged;
       if (tid < 64) {
         // the last tile of a diagonal item waits for the chain; collect the partial sums
         // of the other segments first (they are normally ready by then)
@@ -241,52 +251,63 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
             ok = poll_value<C>(t.ptag + ((trow * t.maxseg + s) * 64 + tid) * W, tag, &v, t.sync, t.status);
             psum += v;
           }
+        // the words were loaded one tile earlier; poll only if they were not yet published
         C v = (C)0;
-        const int q = e.q0 + l;
-        const int J = e.bwd ? e.T - 1 - q : q;
-        if (ok) ok = poll_value<C>(t.ytag + (m.row_off + 64 * J + tid) * W, tag, &v, t.sync, t.status);
-        yb[tid] = v;
+        if (ok && !Tagged<C>::check(pre, tag, &v)) ok = poll_value<C>(ywords(l), tag, &v, t.sync, t.status);
+        yb[l & 1][tid] = v;
+        if (l + 1 < e.nq) pre = Tagged<C>::load(ywords(l + 1));
       }
-      if (!__syncthreads_and(ok)) { bad = true; cc++; break; }
+      if (!__syncthreads_and(ok)) {
+        bad = true;
+        if (tid == 0 && staged) cc++;
+        break;
+      }
+      if (tid == 0) pump();            // every thread is past tile l-1: its stage is free
       const S* tile = (const S*)(smem + (size_t)(cc % NSTAGE) * STAGE);
+      const C* y = yb[l & 1];
 #pragma unroll 8
       for (int c = 32 * half; c < 32 * half + 32; ++c)
-        acc += (C)cvt(tile[Layout<S>::off(r, c)]) * yb[c];
-      __syncthreads();               // stage consumed, yb free again
+        acc += (C)cvt(tile[Layout<S>::off(r, c)]) * y[c];
       cc++;
-      if (tid == 0) pump();
     }
     if (bad) break;
-    red[tid] = acc;
     if (!e.diag) {
+      red[tid] = acc;
       __syncthreads();
       if (tid < 64)
         Tagged<C>::put(t.ptag + ((trow * t.maxseg + e.seg) * 64 + tid) * W, red[tid] + red[tid + 64], tag);
     } else {
       // diagonal block through its inverse: x = Inv (b - off-diagonal products)
+      red[tid] = acc;
       bool ok = true;
       if (e.nq == 0 && tid < 64)        // no own tile (first row of a sweep): no partials
         psum = (C)0;
       C own = rhs;
       if (e.bwd && tid < 64) ok = poll_value<C>(t.ytag + (ro + tid) * W, tag_f, &own, t.sync, t.status);
-      if (!__syncthreads_and(ok)) { bad = true; break; }
-      for (int k = 0; k < PIECES; ++k)          // uniform: wait_stage's result is block-wide
-        if (!wait_stage(cc + k)) { bad = true; break; }
-      if (bad) break;
-      if (tid < 64) yb[tid] = own - ((red[tid] + red[tid + 64]) + psum);
+      int staged = 0;
+      for (int k = 0; k < PIECES && ok; ++k) {
+        const bool sk = stage_ready(cc + k);
+        staged += sk;
+        ok = sk;
+      }
+      if (!__syncthreads_and(ok)) {
+        bad = true;
+        if (tid == 0) cc += staged;
+        break;
+      }
+      if (tid < 64) xb[tid] = own - ((red[tid] + red[tid + 64]) + psum);
       __syncthreads();
       C part = (C)0;
 #pragma unroll 8
       for (int c = 32 * half; c < 32 * half + 32; ++c) {
         const int el = c * 64 + r;                      // column-major inverse element
         const C* piece = (const C*)(smem + (size_t)((cc + el / CPS) % NSTAGE) * STAGE);
-        part += piece[el % CPS] * yb[c];
+        part += piece[el % CPS] * xb[c];
       }
-      __syncthreads();
-      red[tid] = part;
+      red2[tid] = part;
       __syncthreads();
       if (tid < 64) {
-        const C x = red[tid] + red[tid + 64];
+        const C x = red2[tid] + red2[tid + 64];
         Tagged<C>::put(t.ytag + (ro + tid) * W, x, tag);
         if (e.bwd) {
           const int s = t.scatter[ro + tid];
