@@ -307,6 +307,16 @@ cpm_status oras_stationary_solve(const oras_precond* pc, const double* f_dev, do
  * INVALID_ARG (n < 0, NULL pointers with n > 0), CUDA. */
 cpm_status cpm_vec_axpby(int64_t n, double a, const double* x_dev, double b, double* y_dev, void* stream);
 
+/* Failure-detection check of the bounded device waits; no counterpart in the paper.  Launches
+ * one kernel in which a thread waits on an mbarrier phase that nothing completes and on a
+ * device flag that nothing sets, each bounded by limit_s seconds (0 < limit_s <= 10); the
+ * expired waits latch the timeout bit in pc's device status word, as an expired wait inside
+ * the solve or factorisation kernels does, and the kernel returns normally (no fault, the
+ * context stays usable).  Synchronises.  Returns CPM_ERR_TIMEOUT when both waits expired
+ * (the expected outcome; oras_check_status then reports and clears it), CPM_OK if a wait
+ * completed, INVALID_ARG or CUDA otherwise. */
+cpm_status cpm_selftest_bounded_wait(oras_precond* pc, double limit_s, void* stream);
+
 void oras_destroy(oras_precond* pc);
 
 const char* cpm_status_string(cpm_status s);

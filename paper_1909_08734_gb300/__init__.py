@@ -32,6 +32,11 @@ class CpmError(RuntimeError):
         super().__init__(f"{where}: {name}: {msg}")
 
 
+# outcomes reported per right-hand side (returned in the result list when not raising)
+_PER_RHS_STATUS = (_capi.CPM_ERR_NOT_CONVERGED, _capi.CPM_ERR_BREAKDOWN, _capi.CPM_ERR_NAN,
+                   _capi.CPM_ERR_TIMEOUT)
+
+
 def _check(st: int, where: str):
     if st != 0:
         raise CpmError(st, where)
@@ -292,7 +297,7 @@ def cpm_gmres_solve(pc: Preconditioner, f, u, nrhs: int = 1, restart: int = 50, 
     st = _capi.load().cpm_gmres_solve(pc.handle, _dev_ptr(f, n, "f"), _dev_ptr(u, n, "u"), int(nrhs),
                                       C.byref(opts), res, _stream_ptr(stream))
     out = [{"iterations": r.iterations, "relres": r.relres, "status": r.status} for r in res]
-    if st != 0 and (raise_on_failure or st not in (_capi.CPM_ERR_NOT_CONVERGED,)):
+    if st != 0 and (raise_on_failure or st not in _PER_RHS_STATUS):
         raise CpmError(st, "cpm_gmres_solve")
     return out
 
@@ -306,7 +311,7 @@ def oras_stationary_solve(pc: Preconditioner, f, u, nrhs: int = 1, tol: float = 
                                             int(nrhs), float(tol), int(max_it), res,
                                             _stream_ptr(stream))
     out = [{"iterations": r.iterations, "relres": r.relres, "status": r.status} for r in res]
-    if st != 0 and (raise_on_failure or st not in (_capi.CPM_ERR_NOT_CONVERGED,)):
+    if st != 0 and (raise_on_failure or st not in _PER_RHS_STATUS):
         raise CpmError(st, "oras_stationary_solve")
     return out
 
@@ -316,6 +321,11 @@ def cpm_vec_axpby(a: float, x, b: float, y, n: int | None = None, stream=None):
     n = y.numel() if n is None else int(n)
     _check(_capi.load().cpm_vec_axpby(n, float(a), _dev_ptr(x, n, "x"), float(b), _dev_ptr(y, n, "y"),
                                       _stream_ptr(stream)), "cpm_vec_axpby")
+
+
+def cpm_selftest_bounded_wait(pc: Preconditioner, limit_s: float = 0.2, stream=None) -> int:
+    """Let a bounded device wait expire on purpose; returns the status (CPM_ERR_TIMEOUT)."""
+    return int(_capi.load().cpm_selftest_bounded_wait(pc.handle, float(limit_s), _stream_ptr(stream)))
 
 
 def status_string(code: int) -> str:

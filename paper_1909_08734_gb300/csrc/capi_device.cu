@@ -923,6 +923,35 @@ cpm_status cpm_vec_axpby(int64_t n, double a, const double* x_dev, double b, dou
   return CPM_OK;
 }
 
+cpm_status cpm_selftest_bounded_wait(oras_precond* pc, double limit_s, void* stream) {
+  if (!pc || !(limit_s > 0.0) || limit_s > 10.0) {
+    cpm::set_error("cpm_selftest_bounded_wait: need a handle and 0 < limit_s <= 10");
+    return CPM_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* never = nullptr;
+  int* out = nullptr;
+  CK(cudaMalloc(&never, 16));
+  cudaError_t e = cudaMalloc(&out, 16);
+  if (e != cudaSuccess) {
+    cudaFree(never);
+    return cuda_fail(e, "cudaMalloc");
+  }
+  int h[2] = {1, 1};
+  e = cudaMemsetAsync(never, 0, 16, s);
+  if (e == cudaSuccess) e = launch_bounded_wait_selftest((uint64_t)(limit_s * 1e9), never, pc->status, out, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(never);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "cpm_selftest_bounded_wait");
+  if (h[0] == 0 && h[1] == 0) {
+    cpm::set_error("cpm_selftest_bounded_wait: both bounded waits expired (expected)");
+    return CPM_ERR_TIMEOUT;
+  }
+  return CPM_OK;
+}
+
 void oras_destroy(oras_precond* pc) { delete pc; }
 
 }  // extern "C"

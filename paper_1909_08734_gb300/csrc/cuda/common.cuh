@@ -113,12 +113,13 @@ constexpr uint64_t MBAR_WAIT_LIMIT_NS = 2000000000ull;
 // Bounded wait for a phase of an mbarrier; returns false after the time limit.  try_wait
 // suspends the thread in hardware until the phase completes or a short window passes, so
 // the loop polls without sleeping (a sleep would add its granularity to every wait).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = MBAR_WAIT_LIMIT_NS) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 31) == 0 && global_ns() - t0 > MBAR_WAIT_LIMIT_NS) return false;
+    if ((it & 31) == 0 && global_ns() - t0 > limit_ns) return false;
   }
 }
 

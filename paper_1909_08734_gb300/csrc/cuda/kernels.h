@@ -43,6 +43,10 @@ constexpr int KERNELS_BEGIN = 1;
 constexpr int KERNELS_RESTART_UPDATE = 2;
 constexpr int KERNELS_RESIDUAL_CHECK = 2;
 
+// ---- expiry of the bounded waits (test entry point) ----
+cudaError_t launch_bounded_wait_selftest(uint64_t limit_ns, const uint32_t* never, int* status, int* out,
+                                         cudaStream_t s);
+
 // ---- stationary (O)RAS solver vectors ----
 constexpr int KERNELS_AXPY = 1;
 constexpr int KERNELS_NORM2 = 2;

@@ -1,0 +1,62 @@
+"""Failure detection on the GPU without a GPU fault (needs a GB300).
+
+* A bounded device wait is made to expire (an mbarrier phase and a flag that nothing
+  completes): the kernel returns, the handle's status reports CPM_ERR_TIMEOUT once, and the
+  same context then solves normally.
+* A NaN in the right-hand side is reported as CPM_ERR_NAN by FGMRES and by the stationary
+  solver, and the next solve on the same handle succeeds.
+"""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import paper_1909_08734_gb300 as G  # noqa: E402
+from paper_1909_08734_gb300 import _capi  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    band = G.cpm_build_band("sphere", 1.0, 0.0, 0.1, 3)
+    part = G.cpm_partition(band, 8, None, 2)
+    return G.oras_setup(band, part, 1.0, "oras", 4.0, 40.0, "fp32")
+
+
+def _f(pc):
+    cp = pc.band.info()["cp"][: pc.n_active]
+    return torch.tensor(13.0 * cp[:, 0] * cp[:, 1] * cp[:, 2], dtype=torch.float64, device="cuda")
+
+
+def test_expired_wait_is_reported_and_context_survives(pc):
+    t0 = time.time()
+    st = G.cpm_selftest_bounded_wait(pc, 0.2)
+    dt = time.time() - t0
+    assert st == _capi.CPM_ERR_TIMEOUT
+    assert 0.2 <= dt < 10.0
+    with pytest.raises(G.CpmError) as e:
+        G.oras_check_status(pc)
+    assert e.value.status == _capi.CPM_ERR_TIMEOUT
+    G.oras_check_status(pc)                       # reported once, then cleared
+    f = _f(pc)
+    u = torch.zeros_like(f)
+    res = G.cpm_gmres_solve(pc, f, u, tol=1e-8)[0]
+    assert res["status"] == 0 and res["relres"] <= 1e-8
+
+
+def test_nan_rhs_is_reported(pc):
+    f = _f(pc)
+    bad = f.clone()
+    bad[17] = float("nan")
+    u = torch.zeros_like(f)
+    res = G.cpm_gmres_solve(pc, bad, u, tol=1e-8, raise_on_failure=False)[0]
+    assert res["status"] == _capi.CPM_ERR_NAN
+    res = G.oras_stationary_solve(pc, bad, u, tol=1e-8, max_it=10, raise_on_failure=False)[0]
+    assert res["status"] == _capi.CPM_ERR_NAN
+    with pytest.raises(G.CpmError) as e:
+        G.cpm_gmres_solve(pc, bad, u, tol=1e-8)
+    assert e.value.status == _capi.CPM_ERR_NAN
+    res = G.cpm_gmres_solve(pc, f, u, tol=1e-8)[0]
+    assert res["status"] == 0 and np.isfinite(u.cpu().numpy()).all()
