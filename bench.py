@@ -461,6 +461,45 @@ def run_serving(args):
     print(json.dumps(out), flush=True)
 
 
+# Sec. 6.5, subdomain-count table: iterations to a 10^6 residual reduction, unit sphere,
+# p = 2, h = 1/100 (N_A = 654,630), N_O = 4, alpha = 4, alpha_x = 40
+PAPER_SUBDOMAIN_TABLE = {32: (500, 245, 53, 33), 64: (704, 278, 57, 46), 96: (818, 405, 59, 49)}
+
+
+def run_subdomain_table(args):
+    """Iteration counts of RAS / ORAS as solver and preconditioner against the paper's table
+    (no bench line).  Factors in FP32 (the iteration counts match FP64 factors to within
+    one iteration on the bench workload)."""
+    import torch
+    import paper_1909_08734_gb300 as G
+    h, p = 0.01, 2
+    band = G.cpm_build_band("sphere", 1.0, 0.0, h, p)
+    n = band.info()["n_active"]
+    cp = band.info()["cp"][:n]
+    f = torch.tensor((1.0 + 12.0) * cp[:, 0] * cp[:, 1] * cp[:, 2], dtype=torch.float64, device="cuda")
+    out = {"mode": "subdomain_table", "surface": "unit sphere", "h": h, "p": p, "N_A": n, "overlap": 4,
+           "tol": 1e-6, "factors": args.precision, "rows": []}
+    for ns in [int(x) for x in args.table_subdomains.split(",")]:
+        part = G.cpm_partition(band, ns, None, 4)
+        row = {"n_sub": ns, "paper_ras_solver_ras_prec_oras_solver_oras_prec":
+               [PAPER_SUBDOMAIN_TABLE.get(ns, (None,) * 4)[i] for i in (0, 2, 1, 3)]}
+        for method in ("ras", "oras"):
+            t0 = time.time()
+            pc = G.oras_setup(band, part, 1.0, method, 4.0, 40.0, args.precision)
+            setup_s = time.time() - t0
+            u = torch.zeros_like(f)
+            st = G.oras_stationary_solve(pc, f, u, tol=1e-6, max_it=3000, raise_on_failure=False)[0]
+            gm = G.cpm_gmres_solve(pc, f, u, tol=1e-6, max_it=2000, raise_on_failure=False)[0]
+            row[method] = {"solver": st["iterations"], "solver_status": st["status"],
+                           "preconditioner": gm["iterations"], "setup_s": round(setup_s, 2),
+                           "factor_gb": round(pc.info()["factor_bytes"] / 1e9, 2)}
+            del pc
+            torch.cuda.empty_cache()
+        out["rows"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -478,6 +517,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-load", default="0.7", help="offered load(s), fractions of capacity")
     ap.add_argument("--serving-precisions", default="fp32,fp64")
+    ap.add_argument("--subdomain-table", action="store_true",
+                    help="iteration counts against the paper's subdomain-count table")
+    ap.add_argument("--table-subdomains", default="32,64,96")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
@@ -485,6 +527,8 @@ def main():
         run_kernel_only(args)
     elif args.serving:
         run_serving(args)
+    elif args.subdomain_table:
+        run_subdomain_table(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
