@@ -476,8 +476,8 @@ cpm_status launch_iteration(oras_precond* pc, cudaStream_t s) {
   IndirectVec vk{g.V, 0, g.ist, g.n, 0};
   IndirectVec zk{g.Z, 0, g.ist, g.n, 0};
   CK(launch_trsv(pc->trsv, vk, zk, done, s));
-  CK(launch_apply(pc->op, zk, pc->g_vext, nullptr, direct(g.w, 0), 1, 0, done, s));
-  CK(launch_cgs2_and_givens(g, s));
+  CK(launch_ext_values(pc->op, zk, pc->g_vext, 1, done, s));
+  CK(launch_cgs2_and_givens(g, pc->op, zk, pc->g_vext, s));
   pc->launches += KERNELS_PER_ITERATION;
   return CPM_OK;
 }

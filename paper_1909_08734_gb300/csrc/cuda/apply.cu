@@ -69,14 +69,22 @@ __global__ void __launch_bounds__(256) nbr_sum_kernel(const int32_t* __restrict_
   yv[i] = mode ? f[(int64_t)blockIdx.y * n_active + i] - ax : ax;
 }
 
-cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
-                         IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s) {
+cudaError_t launch_ext_values(const OperatorDev& op, IndirectVec x, double* v_scratch, int nrhs, const int* done,
+                              cudaStream_t s) {
   const int64_t n = op.n_nodes;
   dim3 g1((unsigned)((n * 4 + 255) / 256), nrhs);
   if (op.P == 4)
     ext_values_kernel<4><<<g1, 256, 0, s>>>(op.pencil, op.wts, x, v_scratch, n, op.n_active, done);
   else
     ext_values_kernel<3><<<g1, 256, 0, s>>>(op.pencil, op.wts, x, v_scratch, n, op.n_active, done);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
+                         IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s) {
+  const int64_t n = op.n_nodes;
+  cudaError_t e = launch_ext_values(op, x, v_scratch, nrhs, done, s);
+  if (e != cudaSuccess) return e;
   dim3 g2((unsigned)((op.n_active + 255) / 256), nrhs);
   nbr_sum_kernel<<<g2, 256, 0, s>>>(op.nbr, x, v_scratch, f, y, op.n_active, n, op.diag, op.invh2,
                                     mode, done);

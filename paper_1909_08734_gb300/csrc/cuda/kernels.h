@@ -37,8 +37,9 @@ struct OperatorDev {
 // kernels issued by each launcher (for the handle's launch counter)
 constexpr int KERNELS_APPLY = 2;
 constexpr int KERNELS_TRSV = 1;
-constexpr int KERNELS_CGS2_GIVENS = 4;
-constexpr int KERNELS_PER_ITERATION = KERNELS_TRSV + KERNELS_APPLY + KERNELS_CGS2_GIVENS;
+constexpr int KERNELS_EXT_VALUES = 1;
+constexpr int KERNELS_CGS2_GIVENS = 4;   // operator second half fused into the first of them
+constexpr int KERNELS_PER_ITERATION = KERNELS_TRSV + KERNELS_EXT_VALUES + KERNELS_CGS2_GIVENS;
 constexpr int KERNELS_BEGIN = 1;
 constexpr int KERNELS_RESTART_UPDATE = 2;
 constexpr int KERNELS_RESIDUAL_CHECK = 2;
@@ -56,6 +57,9 @@ cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double*
 
 cudaError_t launch_apply(const OperatorDev& op, IndirectVec x, double* v_scratch, const double* f,
                          IndirectVec y, int nrhs, int mode, const int* done, cudaStream_t s);
+// first half of the operator only: v_scratch[k] = (E x)_k for every band node
+cudaError_t launch_ext_values(const OperatorDev& op, IndirectVec x, double* v_scratch, int nrhs, const int* done,
+                              cudaStream_t s);
 
 // ---- local factorisation ----
 struct FactorDev {
@@ -134,7 +138,9 @@ int gmres_state_size(int m);       // doubles of state for restart length m
 int gmres_scalar_offset(int m);     // offset of the scalars (||f||, tol, beta, ||w||, relres)
 cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, double tol, int max_it,
                                cudaStream_t s);
-cudaError_t launch_cgs2_and_givens(const GmresDev& g, cudaStream_t s);
+// After launch_ext_values(z_k) into vext: w = A z_k, CGS2, Givens, v_{k+1} (four kernels).
+cudaError_t launch_cgs2_and_givens(const GmresDev& g, const OperatorDev& op, IndirectVec z, const double* vext,
+                                   cudaStream_t s);
 cudaError_t launch_gmres_restart_update(const GmresDev& g, double* u, cudaStream_t s);
 cudaError_t launch_gmres_residual_check(const GmresDev& g, cudaStream_t s);
 

@@ -53,12 +53,12 @@ __device__ __forceinline__ void block_rows(const GmresDev& g, int64_t* r0, int64
 }
 
 // Block partial sums s[i] (i < cnt, held in shared memory wp[KW][...]) -> part[b][i].
-// Then the last block adds all blocks' partials in block order into out[i].  Returns true
+// Then the last block adds all blocks' partials in a fixed order into out[i].  Returns true
 // in the last block (after out[] is written and visible to that block).
 __device__ bool finish_reduction(const GmresDev& g, double (*wp)[130], int cnt, int ticket,
                                  double* out) {
   __shared__ bool last;
-  __shared__ double gsum[4][130];
+  __shared__ double gsum[1][130];
   for (int i = threadIdx.x; i < cnt; i += KT) {
     double s = 0.0;
     for (int w = 0; w < KW; ++w) s += wp[w][i];
@@ -70,55 +70,82 @@ __device__ bool finish_reduction(const GmresDev& g, double (*wp)[130], int cnt, 
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  // 4 groups of 64 threads: group q adds blocks q, q+4, ...; then the groups in order
-  const int q = threadIdx.x >> 6, i = threadIdx.x & 63;
-  for (int i0 = 0; i0 < cnt; i0 += 64) {
-    if (i0 + i < cnt) {
-      const double* p = g.part + i0 + i;
-      const int64_t ld = g.m + 2;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;   // four loads in flight
-      int b = q;
-      for (; b + 12 < g.nblk; b += 16) {
-        s0 += __ldcg(p + (int64_t)b * ld);
-        s1 += __ldcg(p + (int64_t)(b + 4) * ld);
-        s2 += __ldcg(p + (int64_t)(b + 8) * ld);
-        s3 += __ldcg(p + (int64_t)(b + 12) * ld);
-      }
-      for (; b < g.nblk; b += 4) s0 += __ldcg(p + (int64_t)b * ld);
-      gsum[q][i0 + i] = (s0 + s1) + (s2 + s3);
+  // warp w adds value i = w, w + KW, ...: lane l takes blocks l, l + 32, ... (loads issued
+  // together), then a shuffle tree adds the lanes
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ld = g.m + 2;
+  for (int i = warp; i < cnt; i += KW) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = lane + 32 * u;
+      v[u] = b < g.nblk ? __ldcg(g.part + (int64_t)b * ld + i) : 0.0;
     }
+    double sum = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sum += v[u];
+    for (int b = lane + 256; b < g.nblk; b += 32) sum += __ldcg(g.part + (int64_t)b * ld + i);
+    sum = warp_sum(sum);
+    if (lane == 0) gsum[0][i] = sum;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < cnt; t += KT) out[t] = ((gsum[0][t] + gsum[1][t]) + gsum[2][t]) + gsum[3][t];
+  for (int t = threadIdx.x; t < cnt; t += KT) out[t] = gsum[0][t];
   if (threadIdx.x == 0) g.ist[ticket] = 0;
   __syncthreads();
   return true;
 }
 
-// h1 = V_k^T w
-__global__ void __launch_bounds__(KT) dots_kernel(GmresDev g) {
-  if (cycle_done(g)) return;
-  __shared__ double wp[KW][130];
-  const int k = g.ist[I_K];
-  int64_t r0, r1;
-  block_rows(g, &r0, &r1);
+constexpr int RU = 4;                   // rows per thread processed together (loads in flight)
+
+// wp[warp][i] = this warp's share of sum_rows V[i][row] w[row], i <= k, own rows
+__device__ __forceinline__ void block_dots(const GmresDev& g, int k, int64_t r0, int64_t r1,
+                                           double (*wp)[130]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = 0; i0 <= k; i0 += ILP) {
     double acc[ILP];
 #pragma unroll
     for (int u = 0; u < ILP; ++u) acc[u] = 0.0;
-    for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-      const double w = g.w[row];
+    for (int64_t base = r0 + threadIdx.x; base < r1; base += RU * KT) {
+      double wv[RU], vv[RU][ILP];
 #pragma unroll
-      for (int u = 0; u < ILP; ++u)
-        if (i0 + u <= k) acc[u] += g.V[(int64_t)(i0 + u) * g.n + row] * w;
+      for (int q = 0; q < RU; ++q) {
+        const int64_t row = base + (int64_t)q * KT;
+        wv[q] = row < r1 ? g.w[row] : 0.0;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u)
+          vv[q][u] = (row < r1 && i0 + u <= k) ? g.V[(int64_t)(i0 + u) * g.n + row] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < RU; ++q)
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) acc[u] += vv[q][u] * wv[q];
     }
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
-      const double s = warp_sum(acc[u]);
-      if (lane == 0 && i0 + u <= k) wp[warp][i0 + u] = s;
+      const double sum = warp_sum(acc[u]);
+      if (lane == 0 && i0 + u <= k) wp[warp][i0 + u] = sum;
     }
   }
+}
+
+// w = A z_k on this block's rows (the operator's second half, the same arithmetic as
+// nbr_sum_kernel), then h1 = V_k^T w
+__global__ void __launch_bounds__(KT) dots_kernel(GmresDev g, const int32_t* __restrict__ nbr, IndirectVec z,
+                                                  const double* __restrict__ vext, double diag, double invh2) {
+  if (cycle_done(g)) return;
+  __shared__ double wp[KW][130];
+  const int k = g.ist[I_K];
+  int64_t r0, r1;
+  block_rows(g, &r0, &r1);
+  const double* zk = z.ptr(0);
+  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
+    const int32_t* nb = nbr + 6 * row;
+    double sn = 0.0;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) sn += vext[__ldg(nb + m)];
+    g.w[row] = diag * zk[row] - invh2 * sn;
+  }
+  block_dots(g, k, r0, r1, wp);
   __syncthreads();
   const SL L{g.m};
   finish_reduction(g, wp, k + 1, I_TICKET + 0, g.st + L.h1());
@@ -137,37 +164,39 @@ __global__ void __launch_bounds__(KT) update_kernel(GmresDev g, int h_off, int d
   int64_t r0, r1;
   block_rows(g, &r0, &r1);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-    double a[ILP];
+  for (int64_t base = r0 + threadIdx.x; base < r1; base += RU * KT) {
+    double a[RU][ILP];
 #pragma unroll
-    for (int u = 0; u < ILP; ++u) a[u] = 0.0;
-    for (int i0 = 0; i0 <= k; i0 += ILP)
+    for (int q = 0; q < RU; ++q)
 #pragma unroll
-      for (int u = 0; u < ILP; ++u)
-        if (i0 + u <= k) a[u] += g.V[(int64_t)(i0 + u) * g.n + row] * hs[i0 + u];
-    double s = 0.0;
+      for (int u = 0; u < ILP; ++u) a[q][u] = 0.0;
+    for (int i0 = 0; i0 <= k; i0 += ILP) {
+      double vv[RU][ILP];
 #pragma unroll
-    for (int u = 0; u < ILP; ++u) s += a[u];
-    g.w[row] -= s;
+      for (int q = 0; q < RU; ++q) {
+        const int64_t row = base + (int64_t)q * KT;
+#pragma unroll
+        for (int u = 0; u < ILP; ++u)
+          vv[q][u] = (row < r1 && i0 + u <= k) ? g.V[(int64_t)(i0 + u) * g.n + row] : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < RU; ++q)
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) a[q][u] += vv[q][u] * hs[min(i0 + u, k)];
+    }
+#pragma unroll
+    for (int q = 0; q < RU; ++q) {
+      const int64_t row = base + (int64_t)q * KT;
+      double sum = 0.0;
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) sum += a[q][u];
+      if (row < r1) g.w[row] -= sum;
+    }
   }
   const SL L{g.m};
   if (dots) {
-    for (int i0 = 0; i0 <= k; i0 += ILP) {
-      double acc[ILP];
-#pragma unroll
-      for (int u = 0; u < ILP; ++u) acc[u] = 0.0;
-      for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-        const double w = g.w[row];
-#pragma unroll
-        for (int u = 0; u < ILP; ++u)
-          if (i0 + u <= k) acc[u] += g.V[(int64_t)(i0 + u) * g.n + row] * w;
-      }
-#pragma unroll
-      for (int u = 0; u < ILP; ++u) {
-        const double s = warp_sum(acc[u]);
-        if (lane == 0 && i0 + u <= k) wp[warp][i0 + u] = s;
-      }
-    }
+    __syncthreads();
+    block_dots(g, k, r0, r1, wp);
     __syncthreads();
     finish_reduction(g, wp, k + 1, I_TICKET + 1, g.st + L.h2());
     return;
@@ -343,9 +372,10 @@ cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, double tol, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_cgs2_and_givens(const GmresDev& g, cudaStream_t s) {
+cudaError_t launch_cgs2_and_givens(const GmresDev& g, const OperatorDev& op, IndirectVec z, const double* vext,
+                                   cudaStream_t s) {
   const SL L{g.m};
-  dots_kernel<<<g.nblk, KT, 0, s>>>(g);
+  dots_kernel<<<g.nblk, KT, 0, s>>>(g, op.nbr, z, vext, op.diag, op.invh2);
   update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h1(), 1);
   update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h2(), 0);
   scale_kernel<<<vec_blocks(g.n), KT, 0, s>>>(g);
