@@ -122,9 +122,12 @@ void cpm_band_destroy(cpm_band* band);
  * (active part and the Robin ghost layer), Lambda_j, the nearest Lambda_j point of every
  * boundary node (ties: lowest generator index) and the cross-point marks (boundary nodes
  * within 2*n_overlap*h of a node with neighbours in >= 2 other subdomains).
- * align_passes must be 0 (interface alignment of Sec. 3.2 is not built).
+ * align_passes (0..64) interface-alignment passes (Sec. 3.2) follow the split: an active
+ * node with an active 6-neighbour of another label moves to the label of the grid node
+ * nearest to its closest point (floor(CP/h + 0.5) per axis), all moves of a pass decided on
+ * the labels before it; the paper uses p + 1 passes.
  * Errors: INVALID_ARG (n_sub < 1, n_overlap < 0, a leaf weight <= 0, a subdomain left
- * empty, align_passes != 0), OOM.  Host only. */
+ * empty, align_passes outside 0..64), OOM.  Host only. */
 cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
                          int n_overlap, int align_passes, cpm_part** out);
 /* Labels of the N_A actives (host, int32, valid until destroy). */

@@ -5,6 +5,10 @@ points of Sigma_A.  At a bisection-tree node holding n points and leaves [l0, l1
   axis = the coordinate of largest extent of the points' CP bounding box (ties: x < y < z);
   points ordered by (CP[axis], global index);
   left leaves [l0, l0 + P//2), n_left = floor(n * W_left / W) with integer leaf weights.
+Interface alignment (Sec. 3.2), optional passes after the split: an interface node (an
+  active node with an active 6-neighbour of another label) whose nearest grid point to its
+  closest point, round(CP/h) = floor(CP/h + 0.5) per axis, carries another label moves to
+  that label; all moves of a pass are decided on the labels before the pass.
 Overlap (Sec. 4.1): Sigma_j = active nodes within N_O steps of the disjoint set in the
   6-neighbour graph on Sigma_A; the last layer is BFS distance exactly N_O.
 Sigma_j^G (Sec. 4.1): ghost nodes among the 6-neighbours of Sigma_j.
@@ -50,6 +54,23 @@ def rcb(points: np.ndarray, n_sub: int, leaf_weights=None) -> np.ndarray:
         stack.append((sidx[nL:], l0 + PL, l1))
         stack.append((sidx[:nL], l0, l0 + PL))
     return labels
+
+
+def align_interfaces(band, labels: np.ndarray, passes: int) -> np.ndarray:
+    """Labels after `passes` interface-alignment passes (Sec. 3.2)."""
+    lab = np.asarray(labels, dtype=np.int64).copy()
+    n_a = band.n_active
+    near = np.floor(band.cp[:n_a] / band.h + 0.5).astype(np.int64)     # nearest grid point
+    target_node = band.lookup(near)
+    for _ in range(passes):
+        nb = band.nbr                                               # (N_A, 6), ghosts >= n_a
+        act = nb < n_a
+        nl = np.where(act, lab[np.minimum(nb, n_a - 1)], -1)
+        interface = np.any(act & (nl != lab[:, None]), axis=1)
+        ok = interface & (target_node >= 0) & (target_node < n_a)
+        tgt = np.where(ok, lab[np.clip(target_node, 0, n_a - 1)], lab)
+        lab = np.where(ok, tgt, lab)
+    return lab
 
 
 @dataclasses.dataclass

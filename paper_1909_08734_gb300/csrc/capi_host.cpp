@@ -101,13 +101,13 @@ cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_we
     return CPM_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (align_passes != 0) {
-    cpm::set_error("cpm_partition: interface alignment passes are not supported (use 0)");
+  if (align_passes < 0 || align_passes > 64) {
+    cpm::set_error("cpm_partition: need 0 <= align_passes <= 64");
     return CPM_ERR_INVALID_ARG;
   }
   try {
     cpm_part* p = new cpm_part();
-    cpm_status st = cpm::build_partition(band->b, n_sub, leaf_weights, n_overlap, p->p);
+    cpm_status st = cpm::build_partition(band->b, n_sub, leaf_weights, n_overlap, align_passes, p->p);
     if (st != CPM_OK) {
       delete p;
       return st;

@@ -106,7 +106,7 @@ cpm_status build_band(const Surface& s, double h, int p, double lam_over_h, Band
 // Frees the band's device copies (defined with the CUDA code).
 void band_release_device(Band& b);
 cpm_status build_partition(const Band& band, int n_sub, const int64_t* weights, int n_overlap,
-                           Partition& out);
+                           int align_passes, Partition& out);
 cpm_status build_local_coo(const Band& band, const Partition& part, double c, int transmission,
                            double alpha, double alpha_x, int j, LocalCOO& out);
 

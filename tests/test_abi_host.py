@@ -49,14 +49,17 @@ def test_invalid_arguments_are_reported():
     with pytest.raises(G.CpmError):
         G.cpm_partition(band, 4, [1, 2, 0, 4], 2)
     with pytest.raises(G.CpmError):
-        G.cpm_partition(band, 4, None, 2, align_passes=1)
+        G.cpm_partition(band, 4, None, 2, align_passes=-1)
+    with pytest.raises(G.CpmError):
+        G.cpm_partition(band, 4, None, 2, align_passes=65)
 
 
 CASES = [("sphere", 1.0, 0.0, 0.1, 3, 8, 2, None),
          ("sphere", 1.0, 0.0, 0.1, 2, 6, 3, None),
          ("torus", 1.0, 0.4, 0.05, 3, 16, 2, [256, 1024, 300, 500, 999, 700, 260, 800,
                                              400, 410, 420, 1000, 256, 257, 900, 333]),
-         ("trimesh", 0.0, 0.0, 0.05, 3, 8, 2, None)]
+         ("trimesh", 0.0, 0.0, 0.05, 3, 8, 2, None),
+         ("sphere", 1.0, 0.0, 0.1, 2, 6, 3, "align3")]
 
 
 def _mesh(kind):
@@ -64,15 +67,20 @@ def _mesh(kind):
     return perturbed_icosphere(3, 0.15, 4) if kind == "trimesh" else (None, None)
 
 
-@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"{c[0]}-h{c[3]}-p{c[4]}-S{c[5]}")
+@pytest.fixture(scope="module", params=CASES,
+                ids=lambda c: f"{c[0]}-h{c[3]}-p{c[4]}-S{c[5]}" + ("-aligned" if c[7] == "align3" else ""))
 def pair(request):
     kind, R, r, h, p, ns, no, w = request.param
+    align = 3 if w == "align3" else 0               # interface alignment passes (Sec. 3.2)
+    w = None if w == "align3" else w
     V, T = _mesh(kind)
     band = G.cpm_build_band(kind, R, r, h, p, verts=V, tris=T)
-    part = G.cpm_partition(band, ns, w, no)
+    part = G.cpm_partition(band, ns, w, no, align_passes=align)
     OB = ob.build_band(geometry.make_surface(kind, R, r, V, T), h, p)
     E = interp.extension_matrix(OB)
     lab = partition.rcb(OB.cp[:OB.n_active], ns, w)
+    if align:
+        lab = partition.align_interfaces(OB, lab, align)
     return band, part, OB, E, lab, ns, no
 
 

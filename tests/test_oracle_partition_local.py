@@ -207,3 +207,57 @@ def test_dense_and_sparse_local_lu_agree(small):
     r = np.random.default_rng(5).standard_normal(P.band.n_active)
     z1, z2 = P.M.apply(r), Md.apply(r)
     assert np.linalg.norm(z1 - z2) <= 1e-11 * np.linalg.norm(z1)
+
+
+# ---------------------------------------------------------------- interface alignment
+def _align_brute(band, labels, passes):
+    """Sec. 3.2 restated with python loops and a dictionary of grid points."""
+    lab = [int(x) for x in labels]
+    n_a, h = band.n_active, band.h
+    where = {tuple(int(v) for v in band.ijk[g]): g for g in range(n_a)}
+    offs = [(-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+    for _ in range(passes):
+        new = list(lab)
+        for g in range(n_a):
+            i, j, k = (int(v) for v in band.ijk[g])
+            nbl = [lab[where[(i + a, j + b, k + c)]] for a, b, c in offs if (i + a, j + b, k + c) in where]
+            if all(l == lab[g] for l in nbl):
+                continue
+            near = tuple(int(math.floor(float(band.cp[g][a]) / h + 0.5)) for a in range(3))
+            if near in where:
+                new[g] = lab[where[near]]
+        lab = new
+    return np.array(lab)
+
+
+def test_alignment_matches_brute_force_and_keeps_invariants():
+    B = band.build_band(geometry.Sphere(1.0), 0.2, 2)
+    lab0 = partition.rcb(B.cp[:B.n_active], 5)
+    for passes in (1, 3):
+        lab = partition.align_interfaces(B, lab0, passes)
+        assert np.array_equal(lab, _align_brute(B, lab0, passes))
+        assert set(np.unique(lab)) == set(range(5))
+    # one pass changes only nodes that were interface nodes before it
+    lab1 = partition.align_interfaces(B, lab0, 1)
+    nb = B.nbr
+    act = nb < B.n_active
+    iface = np.any(act & (np.where(act, lab0[np.minimum(nb, B.n_active - 1)], -1) != lab0[:, None]), axis=1)
+    assert np.all(iface[lab1 != lab0])
+
+
+def test_alignment_reduces_misaligned_interface_nodes():
+    """After p + 1 passes fewer interface nodes disagree with the label of the grid node
+    nearest to their closest point (the quantity the passes drive down)."""
+    B = band.build_band(geometry.Torus(1.0, 0.4), 0.05, 2)
+    n_a = B.n_active
+    near = B.lookup(np.floor(B.cp[:n_a] / B.h + 0.5).astype(np.int64))
+
+    def misaligned(lab):
+        act = B.nbr < n_a
+        nl = np.where(act, lab[np.minimum(B.nbr, n_a - 1)], -1)
+        iface = np.any(act & (nl != lab[:, None]), axis=1)
+        return int(np.sum(iface & (lab[near] != lab)))
+
+    lab0 = partition.rcb(B.cp[:n_a], 8)
+    lab3 = partition.align_interfaces(B, lab0, 3)
+    assert misaligned(lab3) < misaligned(lab0)
