@@ -111,6 +111,15 @@ typedef struct {
  * some node leaves the active set: lambda too small), OOM.  Host only. */
 cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
                           cpm_band** out);
+/* Algorithmic band (Sec. 2.1: the active nodes are all nodes used for interpolation; the
+ * paper takes this construction for triangulated surfaces and cites its algorithm).
+ * Reading: Sigma_A is the smallest node set that contains the grid nodes within h of the
+ * surface and the (p+1)^3 interpolation stencil of CP(x) for every node x of Sigma_A and
+ * every 6-neighbour x of Sigma_A; ghosts, order and the per-node data are as for
+ * cpm_build_band (lambda is reported as 0).  It is a subset of the default tube band.
+ * Errors: as cpm_build_band; STENCIL if the closure reaches a point without a closest
+ * point.  Host only. */
+cpm_status cpm_build_band_algorithmic(const cpm_surface* surface, double h, int p, cpm_band** out);
 cpm_status cpm_band_info_get(const cpm_band* band, cpm_band_info* out);
 void cpm_band_destroy(cpm_band* band);
 

@@ -3,6 +3,9 @@
 Grid nodes are x = (i, j, k) * h with integer (i, j, k), computed as float(i) * h.
 Tube-radius construction: Sigma_A = { x : ||x - CP(x)||_2 <= lam }.  Sigma_G = the
 6-neighbours of Sigma_A that are not in Sigma_A (nodes completing the 7-point stencils).
+Algorithmic construction (the active nodes are the nodes used for interpolation): the
+smallest set containing the grid nodes within h of the surface and the interpolation
+stencils of CP(x) for its nodes and their 6-neighbours (build_band_algorithmic).
 
 Readings (the paper gives no radius):
   lam = lam_over_h * h with lam_over_h = ((1.0033 * sqrt(3)) * (p + 1)) / 2 by default.
@@ -126,7 +129,46 @@ def count_active(surface, h: float, p: int, lam_over_h: float | None = None) -> 
 
 
 def build_band(surface, h: float, p: int, lam_over_h: float | None = None) -> Band:
+    """Tube-radius band (Sec. 2.1)."""
     ijk_a, cp_a, lam, tri_a = active_nodes(surface, h, p, lam_over_h)
+    return _assemble(surface, h, p, lam, ijk_a, cp_a, tri_a)
+
+
+def build_band_algorithmic(surface, h: float, p: int) -> Band:
+    """Algorithmic band (Sec. 2.1: the active nodes are the nodes used for interpolation).
+
+    Reading: Sigma_A is the smallest node set that contains the seed -- the grid nodes within
+    h of the surface, so every surface point has a seed node next to it -- and the
+    (p+1)^3 interpolation stencil of CP(x) for every x in Sigma_A and every 6-neighbour x of
+    Sigma_A (the ghost nodes need their extension too).  Computed as a closure: process
+    the newly added nodes and their 6-neighbours, add their stencils, repeat."""
+    seed_ijk, _, _, _ = active_nodes(surface, h, p, 1.0)
+    off = np.stack(np.meshgrid(np.arange(p + 1), np.arange(p + 1), np.arange(p + 1), indexing="ij"),
+                   axis=-1).reshape(-1, 3)
+    members = set(map(tuple, seed_ijk.tolist()))
+    processed = set()
+    frontier = np.asarray(seed_ijk, dtype=np.int64)
+    while len(frontier):
+        cand = np.unique(np.concatenate([frontier] + [frontier + o for o in NBR_OFFSETS]), axis=0)
+        cand = np.array([q for q in map(tuple, cand.tolist()) if q not in processed], dtype=np.int64)
+        if len(cand) == 0:
+            break
+        processed.update(map(tuple, cand.tolist()))
+        Y, _ = _cp_tri(surface, cand.astype(np.float64) * h)
+        if np.any(~np.isfinite(Y)):
+            raise ValueError("algorithmic band reaches a point without a closest point")
+        base = np.floor(Y / h - (p - 1) / 2.0).astype(np.int64)
+        sten = np.unique((base[:, None, :] + off[None, :, :]).reshape(-1, 3), axis=0)
+        new = [q for q in map(tuple, sten.tolist()) if q not in members]
+        members.update(new)
+        frontier = np.array(new, dtype=np.int64).reshape(-1, 3)
+    ijk_a = np.array(sorted(members), dtype=np.int64)          # lexicographic, k fastest
+    cp_a, tri_a = _cp_tri(surface, ijk_a.astype(np.float64) * h)
+    return _assemble(surface, h, p, 0.0, ijk_a, cp_a, tri_a)
+
+
+def _assemble(surface, h, p, lam, ijk_a, cp_a, tri_a) -> Band:
+    """Grid, ghosts, neighbour table of a band given its actives in canonical order."""
     n_a = len(ijk_a)
     lo = ijk_a.min(0) - 2
     hi = ijk_a.max(0) + 2

@@ -31,30 +31,38 @@ const char* cpm_status_string(cpm_status s) {
   return "CPM_ERR_UNKNOWN";
 }
 
-cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
-                          cpm_band** out) {
+// Surface of the C ABI -> internal surface (mesh arrays copied).
+static cpm_status read_surface(const cpm_surface* surface, cpm::Surface& s) {
+  s = cpm::Surface{surface->kind, surface->R, surface->r, {}};
+  if (s.kind == CPM_TRIMESH) {
+    if (!surface->verts || !surface->tris || surface->n_verts < 3 || surface->n_tris < 1) {
+      cpm::set_error("cpm_build_band: a triangulated surface needs vertices and triangles");
+      return CPM_ERR_INVALID_ARG;
+    }
+    s.mesh.V.assign(surface->verts, surface->verts + 3 * surface->n_verts);
+    s.mesh.T.assign(surface->tris, surface->tris + 3 * surface->n_tris);
+    for (int32_t v : s.mesh.T)
+      if (v < 0 || v >= surface->n_verts) {
+        cpm::set_error("cpm_build_band: triangle vertex index out of range");
+        return CPM_ERR_INVALID_ARG;
+      }
+  }
+  return CPM_OK;
+}
+
+static cpm_status build_band_common(const cpm_surface* surface, double h, int p, double lambda_over_h,
+                                    bool algorithmic, cpm_band** out) {
   if (!surface || !out) {
     cpm::set_error("cpm_build_band: NULL argument");
     return CPM_ERR_INVALID_ARG;
   }
   *out = nullptr;
   try {
-    cpm::Surface s{surface->kind, surface->R, surface->r, {}};
-    if (s.kind == CPM_TRIMESH) {
-      if (!surface->verts || !surface->tris || surface->n_verts < 3 || surface->n_tris < 1) {
-        cpm::set_error("cpm_build_band: a triangulated surface needs vertices and triangles");
-        return CPM_ERR_INVALID_ARG;
-      }
-      s.mesh.V.assign(surface->verts, surface->verts + 3 * surface->n_verts);
-      s.mesh.T.assign(surface->tris, surface->tris + 3 * surface->n_tris);
-      for (int32_t v : s.mesh.T)
-        if (v < 0 || v >= surface->n_verts) {
-          cpm::set_error("cpm_build_band: triangle vertex index out of range");
-          return CPM_ERR_INVALID_ARG;
-        }
-    }
+    cpm::Surface s;
+    cpm_status st = read_surface(surface, s);
+    if (st != CPM_OK) return st;
     cpm_band* b = new cpm_band();
-    cpm_status st = cpm::build_band(s, h, p, lambda_over_h, b->b);
+    st = algorithmic ? cpm::build_band_algorithmic(s, h, p, b->b) : cpm::build_band(s, h, p, lambda_over_h, b->b);
     if (st != CPM_OK) {
       delete b;
       return st;
@@ -65,6 +73,15 @@ cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double la
     cpm::set_error("cpm_build_band: out of host memory");
     return CPM_ERR_OOM;
   }
+}
+
+cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
+                          cpm_band** out) {
+  return build_band_common(surface, h, p, lambda_over_h, false, out);
+}
+
+cpm_status cpm_build_band_algorithmic(const cpm_surface* surface, double h, int p, cpm_band** out) {
+  return build_band_common(surface, h, p, 0.0, true, out);
 }
 
 cpm_status cpm_band_info_get(const cpm_band* band, cpm_band_info* out) {

@@ -265,19 +265,19 @@ void point_weights(const double y[3], double h, int p, int32_t base[3], double* 
 static const int NBR_OFF[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
                                   {0, 1, 0},  {0, 0, -1}, {0, 0, 1}};
 
-cpm_status build_band(const Surface& s_in, double h, int p, double lam_over_h, Band& B) {
-  const Surface& s = s_in;
+static cpm_status validate_surface(const Surface& s, double h, int p) {
   if (!(h > 0.0) || (p != 2 && p != 3) ||
       (s.kind != CPM_SPHERE && s.kind != CPM_TORUS && s.kind != CPM_TRIMESH) ||
       (s.kind != CPM_TRIMESH && !(s.R > 0.0)) || (s.kind == CPM_TORUS && !(s.r > 0.0 && s.r < s.R))) {
     set_error("cpm_build_band: invalid surface, h or p (p must be 2 or 3)");
     return CPM_ERR_INVALID_ARG;
   }
-  if (!(lam_over_h > 0.0)) lam_over_h = ((1.0033 * std::sqrt(3.0)) * (p + 1)) / 2.0;
-  const double lam = lam_over_h * h;
-  const bool mesh = s.kind == CPM_TRIMESH;
-  Surface S{s.kind, s.R, s.r, {}};
-  double lo[3], hi[3];
+  return CPM_OK;
+}
+
+// Working copy of the surface (mesh bucket grid built) and its bounding box.
+static cpm_status prepare_surface(const Surface& s, double h, Surface& S, double lo[3], double hi[3]) {
+  S = Surface{s.kind, s.R, s.r, {}};
   if (s.kind == CPM_SPHERE) {
     for (int a = 0; a < 3; ++a) { lo[a] = -s.R; hi[a] = s.R; }
   } else if (s.kind == CPM_TORUS) {
@@ -295,6 +295,14 @@ cpm_status build_band(const Surface& s_in, double h, int p, double lam_over_h, B
         hi[a] = std::max(hi[a], S.mesh.V[3 * v + a]);
       }
   }
+  return CPM_OK;
+}
+
+// Grid nodes x with ||x - CP(x)|| <= lam over the bounding box grown by lam, in
+// lexicographic order (slab by slab, i slowest), with their closest points (and triangles).
+static cpm_status enumerate_tube(const Surface& S, const double lo[3], const double hi[3], double h, double lam,
+                                 std::vector<int32_t>& ijk, std::vector<double>& cp, std::vector<int32_t>& tri) {
+  const bool mesh = S.kind == CPM_TRIMESH;
   int64_t imin[3], imax[3];
   for (int a = 0; a < 3; ++a) {
     imin[a] = (int64_t)std::floor((lo[a] - lam) / h) - 1;
@@ -333,7 +341,6 @@ cpm_status build_band(const Surface& s_in, double h, int p, double lam_over_h, B
     dilate(a, b, 0);
     near.swap(b);
   }
-  // enumerate slab by slab (i slowest): actives come out in lexicographic order
   std::vector<std::vector<int32_t>> slab_ijk(ni), slab_tri(ni);
   std::vector<std::vector<double>> slab_cp(ni);
 #pragma omp parallel
@@ -355,7 +362,7 @@ cpm_status build_band(const Surface& s_in, double h, int p, double lam_over_h, B
               continue;
             t = mesh_closest_point(M, x, lam, y, stamp, qid);
             if (t < 0) continue;
-          } else if (!closest_point(s, x, y)) {
+          } else if (!closest_point(S, x, y)) {
             continue;
           }
           double d[3] = {x[0] - y[0], x[1] - y[1], x[2] - y[2]};
@@ -368,16 +375,23 @@ cpm_status build_band(const Surface& s_in, double h, int p, double lam_over_h, B
         }
     }
   }
-  B = Band();
-  B.surf = std::move(S);
-  B.h = h;
-  B.lam = lam;
-  B.p = p;
+  ijk.clear();
+  cp.clear();
+  tri.clear();
   for (int64_t si = 0; si < ni; ++si) {
-    B.ijk.insert(B.ijk.end(), slab_ijk[si].begin(), slab_ijk[si].end());
-    B.cp.insert(B.cp.end(), slab_cp[si].begin(), slab_cp[si].end());
-    B.tri.insert(B.tri.end(), slab_tri[si].begin(), slab_tri[si].end());
+    ijk.insert(ijk.end(), slab_ijk[si].begin(), slab_ijk[si].end());
+    cp.insert(cp.end(), slab_cp[si].begin(), slab_cp[si].end());
+    tri.insert(tri.end(), slab_tri[si].begin(), slab_tri[si].end());
   }
+  return CPM_OK;
+}
+
+// Ghosts, neighbour table and interpolation data of a band whose actives (ijk, cp, tri) are
+// set in canonical order.
+static cpm_status finish_band(Band& B) {
+  const double h = B.h;
+  const int p = B.p;
+  const bool mesh = B.surf.kind == CPM_TRIMESH;
   const int64_t na = (int64_t)B.ijk.size() / 3;
   if (na == 0) {
     set_error("cpm_build_band: empty band");
@@ -428,7 +442,7 @@ cpm_status build_band(const Surface& s_in, double h, int p, double lam_over_h, B
         ok = tr >= 0;
         B.tri[g] = tr;
       } else {
-        ok = closest_point(s, x, y);
+        ok = closest_point(B.surf, x, y);
       }
       if (!ok) bad_ghost++;
       for (int a = 0; a < 3; ++a) {
@@ -473,6 +487,154 @@ cpm_status build_band(const Surface& s_in, double h, int p, double lam_over_h, B
     return CPM_ERR_STENCIL;
   }
   return CPM_OK;
+}
+
+cpm_status build_band(const Surface& s, double h, int p, double lam_over_h, Band& B) {
+  cpm_status st = validate_surface(s, h, p);
+  if (st != CPM_OK) return st;
+  if (!(lam_over_h > 0.0)) lam_over_h = ((1.0033 * std::sqrt(3.0)) * (p + 1)) / 2.0;
+  const double lam = lam_over_h * h;
+  Surface S;
+  double lo[3], hi[3];
+  st = prepare_surface(s, h, S, lo, hi);
+  if (st != CPM_OK) return st;
+  std::vector<int32_t> ijk, tri;
+  std::vector<double> cp;
+  st = enumerate_tube(S, lo, hi, h, lam, ijk, cp, tri);
+  if (st != CPM_OK) return st;
+  B = Band();
+  B.surf = std::move(S);
+  B.h = h;
+  B.lam = lam;
+  B.p = p;
+  B.ijk = std::move(ijk);
+  B.cp = std::move(cp);
+  B.tri = std::move(tri);
+  return finish_band(B);
+}
+
+cpm_status build_band_algorithmic(const Surface& s, double h, int p, Band& B) {
+  cpm_status st = validate_surface(s, h, p);
+  if (st != CPM_OK) return st;
+  Surface S;
+  double lo[3], hi[3];
+  st = prepare_surface(s, h, S, lo, hi);
+  if (st != CPM_OK) return st;
+  const bool mesh = S.kind == CPM_TRIMESH;
+  // seed: grid nodes within h of the surface
+  std::vector<int32_t> seed, seed_tri;
+  std::vector<double> seed_cp;
+  st = enumerate_tube(S, lo, hi, h, h, seed, seed_cp, seed_tri);
+  if (st != CPM_OK) return st;
+  // membership bitmaps over the bounding box grown by a margin wider than any stencil reach
+  const int margin = 2 * (p + 1) + 4;
+  int64_t gmin[3], gdim[3];
+  for (int a = 0; a < 3; ++a) {
+    gmin[a] = (int64_t)std::floor(lo[a] / h) - margin;
+    gdim[a] = (int64_t)std::ceil(hi[a] / h) + margin - gmin[a] + 1;
+  }
+  if (gdim[0] * gdim[1] * gdim[2] > (int64_t)4000000000) {
+    set_error("cpm_build_band: bounding grid too large");
+    return CPM_ERR_INVALID_ARG;
+  }
+  std::vector<uint8_t> member((size_t)(gdim[0] * gdim[1] * gdim[2]), 0), done(member.size(), 0);
+  auto cell = [&](int64_t i, int64_t j, int64_t k) -> int64_t {
+    const int64_t a = i - gmin[0], b = j - gmin[1], c = k - gmin[2];
+    if (a < 0 || b < 0 || c < 0 || a >= gdim[0] || b >= gdim[1] || c >= gdim[2]) return -1;
+    return (a * gdim[1] + b) * gdim[2] + c;
+  };
+  std::vector<int64_t> frontier;
+  for (size_t t = 0; t < seed.size() / 3; ++t) {
+    const int64_t c = cell(seed[3 * t], seed[3 * t + 1], seed[3 * t + 2]);
+    if (c < 0) { set_error("cpm_build_band: algorithmic band leaves its grid"); return CPM_ERR_STENCIL; }
+    if (!member[c]) { member[c] = 1; frontier.push_back(c); }
+  }
+  const int P = p + 1;
+  int bad = 0;
+  while (!frontier.empty() && !bad) {
+    // the new members and their 6-neighbours not processed yet
+    std::vector<int64_t> cand;
+    for (int64_t c : frontier) {
+      const int64_t k = c % gdim[2], j = (c / gdim[2]) % gdim[1], i = c / (gdim[2] * gdim[1]);
+      for (int m = -1; m < 6; ++m) {
+        const int64_t q = m < 0 ? c : cell(i + gmin[0] + NBR_OFF[m][0], j + gmin[1] + NBR_OFF[m][1],
+                                           k + gmin[2] + NBR_OFF[m][2]);
+        if (q < 0) { bad = 1; break; }
+        if (!done[q]) { done[q] = 1; cand.push_back(q); }
+      }
+    }
+    // their interpolation stencils
+    std::vector<std::vector<int64_t>> found(cand.size());
+#pragma omp parallel reduction(+ : bad)
+    {
+      std::vector<int32_t> stamp(mesh ? (size_t)S.mesh.n_tris() : 0, -1);
+      int32_t qid = 0;
+#pragma omp for schedule(dynamic, 256)
+      for (int64_t t = 0; t < (int64_t)cand.size(); ++t) {
+        const int64_t c = cand[t];
+        const int64_t k = c % gdim[2], j = (c / gdim[2]) % gdim[1], i = c / (gdim[2] * gdim[1]);
+        double x[3] = {(double)(i + gmin[0]) * h, (double)(j + gmin[1]) * h, (double)(k + gmin[2]) * h}, y[3];
+        bool ok = mesh ? mesh_closest_point(S.mesh, x, std::numeric_limits<double>::infinity(), y, stamp, qid) >= 0
+                       : closest_point(S, x, y);
+        if (!ok) { bad++; continue; }
+        int32_t b[3];
+        double w[24];
+        point_weights(y, h, p, b, w, w + P, w + 2 * P);
+        for (int a = 0; a < P; ++a)
+          for (int bb = 0; bb < P; ++bb)
+            for (int e = 0; e < P; ++e) {
+              const int64_t q = cell((int64_t)b[0] + a, (int64_t)b[1] + bb, (int64_t)b[2] + e);
+              if (q < 0) { bad++; continue; }
+              found[t].push_back(q);
+            }
+      }
+    }
+    frontier.clear();
+    for (auto& f : found)
+      for (int64_t q : f)
+        if (!member[q]) { member[q] = 1; frontier.push_back(q); }
+  }
+  if (bad) {
+    set_error("cpm_build_band: algorithmic band reaches a point without a closest point or leaves its grid");
+    return CPM_ERR_STENCIL;
+  }
+  // actives in lexicographic order, their closest points
+  B = Band();
+  for (int64_t c = 0; c < (int64_t)member.size(); ++c)
+    if (member[c]) {
+      const int64_t k = c % gdim[2], j = (c / gdim[2]) % gdim[1], i = c / (gdim[2] * gdim[1]);
+      B.ijk.insert(B.ijk.end(), {(int32_t)(i + gmin[0]), (int32_t)(j + gmin[1]), (int32_t)(k + gmin[2])});
+    }
+  const int64_t na = (int64_t)B.ijk.size() / 3;
+  B.cp.resize(3 * na);
+  if (mesh) B.tri.resize(na);
+  int nocp = 0;
+#pragma omp parallel reduction(+ : nocp)
+  {
+    std::vector<int32_t> stamp(mesh ? (size_t)S.mesh.n_tris() : 0, -1);
+    int32_t qid = 0;
+#pragma omp for
+    for (int64_t g = 0; g < na; ++g) {
+      double x[3] = {(double)B.ijk[3 * g] * h, (double)B.ijk[3 * g + 1] * h, (double)B.ijk[3 * g + 2] * h};
+      if (mesh) {
+        const int32_t t = mesh_closest_point(S.mesh, x, std::numeric_limits<double>::infinity(), &B.cp[3 * g],
+                                             stamp, qid);
+        B.tri[g] = t;
+        if (t < 0) nocp++;
+      } else if (!closest_point(S, x, &B.cp[3 * g])) {
+        nocp++;
+      }
+    }
+  }
+  if (nocp) {
+    set_error("cpm_build_band: an active node without a closest point");
+    return CPM_ERR_STENCIL;
+  }
+  B.surf = std::move(S);
+  B.h = h;
+  B.lam = 0.0;
+  B.p = p;
+  return finish_band(B);
 }
 
 }  // namespace cpm

@@ -103,6 +103,9 @@ struct LocalCOO {
 };
 
 cpm_status build_band(const Surface& s, double h, int p, double lam_over_h, Band& out);
+// Algorithmic band: the smallest node set containing the grid nodes within h of the surface
+// and the interpolation stencils of CP(x) for its nodes and their 6-neighbours.
+cpm_status build_band_algorithmic(const Surface& s, double h, int p, Band& out);
 // Frees the band's device copies (defined with the CUDA code).
 void band_release_device(Band& b);
 cpm_status build_partition(const Band& band, int n_sub, const int64_t* weights, int n_overlap,

@@ -59,7 +59,9 @@ CASES = [("sphere", 1.0, 0.0, 0.1, 3, 8, 2, None),
          ("torus", 1.0, 0.4, 0.05, 3, 16, 2, [256, 1024, 300, 500, 999, 700, 260, 800,
                                              400, 410, 420, 1000, 256, 257, 900, 333]),
          ("trimesh", 0.0, 0.0, 0.05, 3, 8, 2, None),
-         ("sphere", 1.0, 0.0, 0.1, 2, 6, 3, "align3")]
+         ("sphere", 1.0, 0.0, 0.1, 2, 6, 3, "align3"),
+         ("sphere", 1.0, 0.0, 0.1, 3, 8, 2, "algorithmic"),
+         ("trimesh", 0.0, 0.0, 0.05, 3, 8, 2, "algorithmic")]
 
 
 def _mesh(kind):
@@ -68,15 +70,19 @@ def _mesh(kind):
 
 
 @pytest.fixture(scope="module", params=CASES,
-                ids=lambda c: f"{c[0]}-h{c[3]}-p{c[4]}-S{c[5]}" + ("-aligned" if c[7] == "align3" else ""))
+                ids=lambda c: f"{c[0]}-h{c[3]}-p{c[4]}-S{c[5]}" + {"align3": "-aligned",
+                                                                     "algorithmic": "-algorithmic"}.get(
+                    c[7] if isinstance(c[7], str) else "", ""))
 def pair(request):
     kind, R, r, h, p, ns, no, w = request.param
     align = 3 if w == "align3" else 0               # interface alignment passes (Sec. 3.2)
-    w = None if w == "align3" else w
+    construction = "algorithmic" if w == "algorithmic" else "tube"
+    w = None if isinstance(w, str) else w
     V, T = _mesh(kind)
-    band = G.cpm_build_band(kind, R, r, h, p, verts=V, tris=T)
+    band = G.cpm_build_band(kind, R, r, h, p, verts=V, tris=T, construction=construction)
     part = G.cpm_partition(band, ns, w, no, align_passes=align)
-    OB = ob.build_band(geometry.make_surface(kind, R, r, V, T), h, p)
+    surf = geometry.make_surface(kind, R, r, V, T)
+    OB = ob.build_band(surf, h, p) if construction == "tube" else ob.build_band_algorithmic(surf, h, p)
     E = interp.extension_matrix(OB)
     lab = partition.rcb(OB.cp[:OB.n_active], ns, w)
     if align:

@@ -232,3 +232,32 @@ def test_tensor_core_lu_matches_cuda_core_lu(torus_uneven, prec, tol):
     ref = oras.M.apply(r.cpu().numpy())
     err_ref = np.linalg.norm(out[0].cpu().numpy() - ref) / np.linalg.norm(ref)
     assert err_ref <= (1e-3 if prec == "fp32" else 5e-2), err_ref
+
+
+def test_algorithmic_band_preconditioner_and_solve():
+    """The whole path on an algorithmic band (smallest interpolation-closed node set)."""
+    from oracle import band as ob, geometry, interp, local, operator, partition, schwarz
+    h, c, ns, no = 0.1, 1.0, 8, 2
+    band = G.cpm_build_band("sphere", 1.0, 0.0, h, 3, construction="algorithmic")
+    part = G.cpm_partition(band, ns, None, no)
+    B = ob.build_band_algorithmic(geometry.Sphere(1.0), h, 3)
+    E = interp.extension_matrix(B)
+    A = operator.cpm_matrix(B, E, c)
+    lab = partition.rcb(B.cp[:B.n_active], ns)
+    marks = partition.CrossMarks(B, partition.cross_point_nodes(B, lab), no)
+    lps = [local.oras_local(B, partition.build_subdomain(B, E, lab, j, no, True), c, 4.0, 40.0, marks)
+           for j in range(ns)]
+    M = schwarz.Schwarz(lps, B.n_active)
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, "fp64")
+    r = random_vector(pc.n_active, 41)
+    z = torch.empty(pc.n_active, dtype=torch.float64, device="cuda")
+    G.oras_apply(pc, _dev(r), z)
+    ref = M.apply(r)
+    assert np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref) <= 1e-10
+    cp = B.cp[:B.n_active]
+    f = (c + 12.0) * cp[:, 0] * cp[:, 1] * cp[:, 2]
+    u = torch.zeros(pc.n_active, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-12)[0]
+    gref = krylov.fgmres(lambda x: A @ x, M.apply, f, 1e-12)
+    assert res["status"] == 0 and abs(res["iterations"] - gref.iterations) <= 1
+    assert np.linalg.norm(u.cpu().numpy() - gref.x) / np.linalg.norm(gref.x) <= 1e-10

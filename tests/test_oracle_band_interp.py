@@ -157,8 +157,9 @@ def test_operator_matrix_free_equals_assembled(small_sphere):
     assert np.allclose(operator.apply(B, E, 1.0, x), A @ x, rtol=0, atol=1e-9)
 
 
-def _xyz_errors(h):
-    B = band.build_band(geometry.Sphere(1.0), h, 3)
+def _xyz_errors(h, construction="tube"):
+    B = (band.build_band(geometry.Sphere(1.0), h, 3) if construction == "tube"
+         else band.build_band_algorithmic(geometry.Sphere(1.0), h, 3))
     E = interp.extension_matrix(B)
     c = 1.0
     A = operator.cpm_matrix(B, E, c)
@@ -180,3 +181,30 @@ def test_xyz_eigenfunction_second_order():
     assert s1 / s2 > 2.7 and s2 / s3 > 3.3
     assert e1 / e2 > 4.0 and e2 / e3 > 4.0
     assert s3 < 1e-4
+
+
+# ---------------------------------------------------------------- algorithmic band
+@pytest.mark.parametrize("surf,h,p", [(geometry.Sphere(1.0), 0.1, 3), (geometry.Torus(1.0, 0.4), 0.1, 2)])
+def test_algorithmic_band_is_the_minimal_interpolation_closure(surf, h, p):
+    A = band.build_band_algorithmic(surf, h, p)
+    actives = set(map(tuple, A.ijk[:A.n_active].tolist()))
+    # closed: every stencil of CP(x), x active or ghost, is active
+    cols, _ = interp.interpolation_rows(A, A.cp)
+    assert cols.min() >= 0 and cols.max() < A.n_active
+    # minimal: every active node is a seed node (within h of the surface) or used by a stencil
+    seed = set(map(tuple, band.active_nodes(surf, h, p, 1.0)[0].tolist()))
+    used = set(map(tuple, A.ijk[np.unique(cols)].tolist()))
+    assert actives == seed | used
+    # and it sits inside the default tube band
+    T = band.build_band(surf, h, p)
+    assert actives <= set(map(tuple, T.ijk[:T.n_active].tolist()))
+    assert A.n_active < T.n_active
+
+
+def test_algorithmic_band_keeps_second_order():
+    # same surface error as the tube band's at h = 0.2, 0.1 (ratio > 2.7, i.e. order > 1.4
+    # in the pre-asymptotic range where the tube band shows the same ratio)
+    s1, _ = _xyz_errors(0.2, "algorithmic")
+    s2, _ = _xyz_errors(0.1, "algorithmic")
+    t2, _ = _xyz_errors(0.1)
+    assert s1 / s2 > 2.7 and s2 < 2.0 * t2
