@@ -324,6 +324,24 @@ def run_native(args):
     e2e = {"value": round(world * 1e3 / e2e_ms, 3), "unit": "solves/s",
            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
 
+    # ---- several right-hand sides per streamed factor tile (after every single-rhs timing:
+    # the first multi-rhs launch grows the solve's tagged-word buffers) ----
+    r8 = torch.randn(8 * n, dtype=torch.float64, device="cuda")
+    z8 = torch.empty_like(r8)
+    for _ in range(3):
+        G.oras_apply(pc, r8, z8, nrhs=8, stream=stream)
+    m0 = torch.cuda.Event(enable_timing=True)
+    m1 = torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(10):
+        G.oras_apply(pc, r8, z8, nrhs=8, stream=stream)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    G.oras_check_status(pc)
+    ms8 = m0.elapsed_time(m1) / 10
+    extra["multi_rhs_apply"] = {"nrhs": 8, "launch_ms": round(ms8, 4), "ms_per_rhs": round(ms8 / 8, 4),
+                                "speedup_per_rhs_vs_single": round(8 * apply_ms / ms8, 2)}
+
     # ---- CPU baseline: the oracle, rank 0 at N = 1 only ----
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

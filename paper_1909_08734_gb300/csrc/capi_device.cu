@@ -167,7 +167,7 @@ cpm_status set_schedule(oras_precond* pc, int ctas_per_sm, int kseg, int prefetc
     t.items = nullptr;
     t.ptag = nullptr;
     const int words = pc->precision == CPM_FP64 ? 2 : 1;
-    const int64_t nslot = (int64_t)words * (pc->rows_total / TILE) * maxseg * TILE;
+    const int64_t nslot = (int64_t)words * (pc->rows_total / TILE) * maxseg * TILE * std::max(1, t.nr_cap);
     int2* d_items;
     uint64_t* d_ptag;
     ALLOC(d_items, int2, items.size());
@@ -410,6 +410,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   t.sync = d_sync;
   t.status = pc->status;
   t.precision = precision;
+  t.nr_cap = 1;
   CK(trsv_prepare(precision));
   st = set_schedule(pc, trsv_ctas_per_sm(precision), 1023, 0, 0);
   if (st != CPM_OK) return st;
@@ -542,69 +543,110 @@ cpm_status ensure_stationary(oras_precond* pc) {
   if (pc->st_z) return CPM_OK;
   const int64_t n = pc->n_active;
   pc->st_nblk = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(pc->device)));
-  ALLOC(pc->st_z, double, n);
-  ALLOC(pc->st_r, double, n);
+  ALLOC(pc->st_z, double, n * TRSV_MAX_NR);
+  ALLOC(pc->st_r, double, n * TRSV_MAX_NR);
   ALLOC(pc->st_part, double, pc->st_nblk);
-  ALLOC(pc->st_norm, double, 2);
-  if (!pc->st_norm_host) CK(cudaMallocHost(&pc->st_norm_host, 2 * sizeof(double)));
+  ALLOC(pc->st_norm, double, TRSV_MAX_NR);
+  if (!pc->st_norm_host) CK(cudaMallocHost(&pc->st_norm_host, TRSV_MAX_NR * sizeof(double)));
   if (!pc->g_vext) ALLOC(pc->g_vext, double, pc->n_nodes);
   return CPM_OK;
 }
 
-// ||x||_2 on the device, returned to the host (one synchronisation).
-cpm_status norm_to_host(oras_precond* pc, const double* x, int slot, double* out, cudaStream_t s) {
-  CK(launch_norm2(x, pc->n_active, pc->st_part, pc->st_nblk, pc->st_norm + slot, s));
-  CK(cudaMemcpyAsync(pc->st_norm_host + slot, pc->st_norm + slot, sizeof(double), cudaMemcpyDeviceToHost, s));
+// ||x_q||_2 for the listed columns (device), returned to the host with one synchronisation.
+cpm_status norms_to_host(oras_precond* pc, const double* x, int64_t ld, const int* cols, int ncols, double* out,
+                         cudaStream_t s) {
+  for (int c = 0; c < ncols; ++c)
+    CK(launch_norm2(x + (int64_t)cols[c] * ld, pc->n_active, pc->st_part, pc->st_nblk, pc->st_norm + cols[c], s));
+  CK(cudaMemcpyAsync(pc->st_norm_host, pc->st_norm, TRSV_MAX_NR * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  pc->launches += KERNELS_NORM2;
-  *out = pc->st_norm_host[slot];
+  pc->launches += (int64_t)KERNELS_NORM2 * ncols;
+  for (int c = 0; c < ncols; ++c) out[cols[c]] = pc->st_norm_host[cols[c]];
   return CPM_OK;
 }
 
-cpm_status stationary_one(oras_precond* pc, const double* f, double* u, double tol, int max_it,
-                          cpm_gmres_result* res, cudaStream_t s) {
+// nr (<= TRSV_MAX_NR) right-hand sides iterated together: one batched solve launch per
+// iteration for all of them; a right-hand side that has converged (or failed) is no longer
+// updated, so each one follows exactly the single right-hand-side sequence of operations.
+cpm_status stationary_batch(oras_precond* pc, const double* f, double* u, int nr, double tol, int max_it,
+                            cpm_gmres_result* res, cudaStream_t s) {
   const int64_t n = pc->n_active;
-  res->iterations = 0;
-  res->relres = 0.0;
-  res->status = CPM_OK;
-  CK(cudaMemsetAsync(u, 0, sizeof(double) * n, s));
-  double nf = 0.0;
-  cpm_status st = norm_to_host(pc, f, 0, &nf, s);
+  double nf[TRSV_MAX_NR] = {0}, nrm[TRSV_MAX_NR] = {0};
+  int act[TRSV_MAX_NR], nact = 0, all[TRSV_MAX_NR];
+  for (int q = 0; q < nr; ++q) all[q] = q;
+  CK(cudaMemsetAsync(u, 0, sizeof(double) * n * nr, s));
+  cpm_status st = norms_to_host(pc, f, n, all, nr, nf, s);
   if (st != CPM_OK) return st;
-  if (!std::isfinite(nf)) {
-    res->status = CPM_ERR_NAN;
-    return CPM_OK;
+  for (int q = 0; q < nr; ++q) {
+    res[q].iterations = 0;
+    res[q].relres = 0.0;
+    res[q].status = CPM_OK;
+    if (!std::isfinite(nf[q])) res[q].status = CPM_ERR_NAN;
+    else if (nf[q] > 0.0) {
+      res[q].status = CPM_ERR_NOT_CONVERGED;
+      act[nact++] = q;
+    }
   }
-  if (nf == 0.0) return CPM_OK;
-  CK(cudaMemcpyAsync(pc->st_r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  res->status = CPM_ERR_NOT_CONVERGED;
-  for (int it = 1; it <= max_it; ++it) {
-    CK(launch_trsv(pc->trsv, direct(pc->st_r, 0), direct(pc->st_z, 0), nullptr, s));
-    CK(launch_axpy(u, pc->st_z, n, pc->st_nblk, s));
-    CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(pc->st_r, 0), 1, 1, nullptr, s));
-    pc->launches += KERNELS_TRSV + KERNELS_AXPY + KERNELS_APPLY;
-    double nr = 0.0;
-    st = norm_to_host(pc, pc->st_r, 1, &nr, s);
+  CK(cudaMemcpyAsync(pc->st_r, f, sizeof(double) * n * nr, cudaMemcpyDeviceToDevice, s));
+  for (int it = 1; it <= max_it && nact > 0; ++it) {
+    CK(launch_trsv(pc->trsv, direct(pc->st_r, n), direct(pc->st_z, n), nullptr, s, nr));
+    pc->launches += KERNELS_TRSV;
+    for (int c = 0; c < nact; ++c) {
+      const int q = act[c];
+      CK(launch_axpy(u + (int64_t)q * n, pc->st_z + (int64_t)q * n, n, pc->st_nblk, s));
+      CK(launch_apply(pc->op, direct(u + (int64_t)q * n, 0), pc->g_vext, f + (int64_t)q * n,
+                      direct(pc->st_r + (int64_t)q * n, 0), 1, 1, nullptr, s));
+      pc->launches += KERNELS_AXPY + KERNELS_APPLY;
+    }
+    st = norms_to_host(pc, pc->st_r, n, act, nact, nrm, s);
     if (st != CPM_OK) return st;
-    res->iterations = it;
-    res->relres = nr / nf;
-    if (!std::isfinite(nr)) {
-      res->status = CPM_ERR_NAN;
-      break;
+    int keep = 0;
+    for (int c = 0; c < nact; ++c) {
+      const int q = act[c];
+      res[q].iterations = it;
+      res[q].relres = nrm[q] / nf[q];
+      if (!std::isfinite(nrm[q])) res[q].status = CPM_ERR_NAN;
+      else if (nrm[q] <= tol * nf[q]) res[q].status = CPM_OK;
+      else act[keep++] = q;
     }
-    if (nr <= tol * nf) {
-      res->status = CPM_OK;
-      break;
-    }
+    nact = keep;
   }
   int dst = 0;
   CK(cudaMemcpy(&dst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (dst & ST_TIMEOUT) {
     CK(cudaMemset(pc->status, 0, sizeof(int)));
-    res->status = CPM_ERR_TIMEOUT;
+    for (int q = 0; q < nr; ++q) res[q].status = CPM_ERR_TIMEOUT;
   }
   return CPM_OK;
 }
+
+// Tagged-word buffers of the batched solve for TRSV_MAX_NR right-hand sides per launch
+// (grown once; drops the captured iteration graph, which holds the old buffers).
+cpm_status ensure_multi_rhs(oras_precond* pc) {
+  TrsvDev& t = pc->trsv;
+  if (t.nr_cap >= TRSV_MAX_NR) return CPM_OK;
+  const int words = pc->precision == CPM_FP64 ? 2 : 1;
+  uint64_t *y = nullptr, *pt = nullptr;
+  const int64_t ny = (int64_t)words * pc->rows_total * TRSV_MAX_NR;
+  const int64_t np = (int64_t)words * (pc->rows_total / TILE) * t.maxseg * TILE * TRSV_MAX_NR;
+  ALLOC(y, uint64_t, ny);
+  ALLOC(pt, uint64_t, np);
+  CK(cudaMemset(y, 0, 8 * (size_t)ny));
+  CK(cudaMemset(pt, 0, 8 * (size_t)np));
+  CK(cudaDeviceSynchronize());
+  pc->release(t.ytag);
+  pc->release(t.ptag);
+  t.ytag = y;
+  t.ptag = pt;
+  t.nr_cap = TRSV_MAX_NR;
+  if (pc->iter_graph) {
+    cudaGraphExecDestroy(pc->iter_graph);
+    pc->iter_graph = nullptr;
+  }
+  return CPM_OK;
+}
+
+// Largest launch width in {8, 4, 2, 1} not above the right-hand sides left.
+int nr_chunk(int left) { return left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1)); }
 
 }  // namespace
 
@@ -718,8 +760,9 @@ cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmissio
   int maxseg = 1;
   trsv_build_items(Ts.data(), ns, 8, 0, items, &maxseg);
   const int words = precision == CPM_FP64 ? 2 : 1;
-  const int64_t sched = rnd(8 * (int64_t)items.size()) + rnd(8 * words * (rows / TILE) * maxseg * TILE) +
-                        rnd(8 * words * rows) + rnd(16);
+  const int64_t nrc = nrhs > 1 ? TRSV_MAX_NR : 1;       // tagged words per row and rhs slot
+  const int64_t sched = rnd(8 * (int64_t)items.size()) + rnd(8 * words * (rows / TILE) * maxseg * TILE * nrc) +
+                        rnd(8 * words * rows * nrc) + rnd(16);
   const int64_t nblk = 152;
   const int64_t gmres = rnd(8 * (restart + 1) * N) + rnd(8 * restart * N) + 2 * rnd(8 * N) +
                         rnd(8 * nblk * (restart + 2)) + rnd(8 * (int64_t)(restart + 2) * (restart + 8) + 4096) +
@@ -766,10 +809,19 @@ cpm_status oras_apply(const oras_precond* pc, const double* r_dev, double* z_dev
     cpm::set_error("oras_apply: bad argument");
     return CPM_ERR_INVALID_ARG;
   }
-  const_cast<oras_precond*>(pc)->launches += nrhs;
-  for (int i = 0; i < nrhs; ++i)
-    CK(launch_trsv(pc->trsv, direct(const_cast<double*>(r_dev) + (int64_t)i * pc->n_active, 0),
-                   direct(z_dev + (int64_t)i * pc->n_active, 0), nullptr, (cudaStream_t)stream));
+  oras_precond* mpc = const_cast<oras_precond*>(pc);
+  if (nrhs > 1) {
+    cpm_status st = ensure_multi_rhs(mpc);
+    if (st != CPM_OK) return st;
+  }
+  const int64_t n = pc->n_active;
+  for (int i = 0; i < nrhs;) {
+    const int nr = nr_chunk(nrhs - i);
+    CK(launch_trsv(pc->trsv, direct(const_cast<double*>(r_dev) + (int64_t)i * n, n), direct(z_dev + (int64_t)i * n, n),
+                   nullptr, (cudaStream_t)stream, nr));
+    mpc->launches += KERNELS_TRSV;
+    i += nr;
+  }
   return CPM_OK;
 }
 
@@ -899,12 +951,20 @@ cpm_status oras_stationary_solve(const oras_precond* cpc, const double* f_dev, d
   }
   cpm_status st = ensure_stationary(pc);
   if (st != CPM_OK) return st;
-  cpm_status first = CPM_OK;
-  for (int i = 0; i < nrhs; ++i) {
-    st = stationary_one(pc, f_dev + (int64_t)i * pc->n_active, u_dev + (int64_t)i * pc->n_active, tol, max_it,
-                        &results[i], (cudaStream_t)stream);
+  if (nrhs > 1) {
+    st = ensure_multi_rhs(pc);
     if (st != CPM_OK) return st;
-    if (first == CPM_OK && results[i].status != CPM_OK) first = (cpm_status)results[i].status;
+  }
+  cpm_status first = CPM_OK;
+  const int64_t n = pc->n_active;
+  for (int i = 0; i < nrhs;) {
+    const int nr = nr_chunk(nrhs - i);
+    st = stationary_batch(pc, f_dev + (int64_t)i * n, u_dev + (int64_t)i * n, nr, tol, max_it, &results[i],
+                          (cudaStream_t)stream);
+    if (st != CPM_OK) return st;
+    for (int q = 0; q < nr; ++q)
+      if (first == CPM_OK && results[i + q].status != CPM_OK) first = (cpm_status)results[i + q].status;
+    i += nr;
   }
   if (first != CPM_OK) cpm::set_error(std::string("oras_stationary_solve: ") + cpm_status_string(first));
   return first;

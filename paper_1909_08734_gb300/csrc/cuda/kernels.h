@@ -110,9 +110,12 @@ struct TrsvDev {
   int* status;
   int precision;           // 0 fp64, 1 fp32, 2 bf16
   int grid;
+  int nr_cap;              // right-hand sides the tagged-word buffers hold per row
 };
+constexpr int TRSV_MAX_NR = 8;
+// nr in {1, 2, 4, 8} right-hand sides (r_in / z_out columns) per launch, nr <= t.nr_cap
 cudaError_t launch_trsv(const TrsvDev& t, IndirectVec r_in, IndirectVec z_out, const int* done,
-                        cudaStream_t s);
+                        cudaStream_t s, int nr = 1);
 int trsv_ctas_per_sm(int precision);
 cudaError_t trsv_prepare(int precision);
 // Queue of work items for the batched solve: forward items, then backward items, each

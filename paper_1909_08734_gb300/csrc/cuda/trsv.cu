@@ -126,7 +126,9 @@ __device__ __forceinline__ Item decode(const TrsvDev& t, int idx) {
   return e;
 }
 
-template <typename S, typename C>
+// NR right-hand sides share every streamed tile (columns NR of IndirectVec r_in / z_out);
+// tagged words are laid out (row, rhs) with NR words per row.
+template <typename S, typename C, int NR>
 __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectVec r_in, IndirectVec z_out,
                                                             const int* done) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -136,9 +138,9 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   constexpr int CPS = STAGE / sizeof(C);                      // C values per stage
   static_assert(PIECES >= 1 && PIECES <= 2 && NSTAGE >= PIECES, "ring too small");
   __shared__ __align__(8) uint64_t bar[NSTAGE];
-  __shared__ C yb[2][64];                                     // solved pieces, double-buffered
-  __shared__ C xb[64];
-  __shared__ C red[TRSV_THREADS], red2[TRSV_THREADS];
+  __shared__ C yb[2][NR][64];                                 // solved pieces, double-buffered
+  __shared__ C xb[NR][64];
+  __shared__ C red[NR][TRSV_THREADS], red2[NR][TRSV_THREADS];
   __shared__ int sh_cur, sh_mb;
   const int tid = threadIdx.x;
   const S* tiles = (const S*)t.tiles;
@@ -151,8 +153,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   const uint32_t epoch = *(volatile uint32_t*)&t.sync[2];
   const uint32_t tag_f = 2u * epoch + 1u, tag_b = 2u * epoch + 2u;
   const bool skip = done && *(volatile const int*)done;
-  const double* rin = r_in.ptr(0);
-  double* zout = z_out.ptr(0);
+
   uint32_t cc = 0;                 // stages consumed (all threads)
   bool bad = false;
   const int r = tid & 63, half = tid >> 6;
@@ -224,21 +225,30 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
     const int64_t ro = m.row_off + 64 * e.I;
     const int64_t trow = (m.row_off >> 6) + e.I;
     const uint32_t tag = e.bwd ? tag_b : tag_f;
-    // restrict: prefetch this row's right-hand side (forward diagonal items)
-    C rhs = (C)0;
+    // restrict: prefetch this row's right-hand sides (forward diagonal items)
+    C rhs[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) rhs[q] = (C)0;
     if (e.diag && !e.bwd && tid < 64) {
       const int g = t.gather[ro + tid];
-      if (g >= 0) rhs = (C)rin[g];
+      if (g >= 0)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) rhs[q] = (C)r_in.ptr(q)[g];
     }
     // tagged words of the solved piece multiplying off-diagonal tile l of this item
-    auto ywords = [&](int l) {
-      const int q = e.q0 + l;
-      const int J = e.bwd ? e.T - 1 - q : q;
-      return t.ytag + (m.row_off + 64 * J + tid) * W;
+    auto ywords = [&](int l, int q) {
+      const int qq = e.q0 + l;
+      const int J = e.bwd ? e.T - 1 - qq : qq;
+      return t.ytag + ((m.row_off + 64 * J + tid) * NR + q) * W;
     };
-    typename Tagged<C>::Raw pre{};
-    if (tid < 64 && e.nq > 0) pre = Tagged<C>::load(ywords(0));
-    C acc = (C)0, psum = (C)0;
+    auto pwords = [&](int seg, int q) { return t.ptag + (((trow * t.maxseg + seg) * 64 + tid) * NR + q) * W; };
+    typename Tagged<C>::Raw pre[NR];
+    if (tid < 64 && e.nq > 0)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) pre[q] = Tagged<C>::load(ywords(0, q));
+    C acc[NR], psum[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = psum[q] = (C)0;
     for (int l = 0; l < e.nq; ++l) {
       const bool staged = stage_ready(cc);
       bool ok = staged;
@@ -246,16 +256,23 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
         // the last tile of a diagonal item waits for the chain; collect the partial sums
         // of the other segments first (they are normally ready by then)
         if (e.diag && l == e.nq - 1)
-          for (int s = 0; s < e.nseg - 1 && ok; ++s) {
-            C v;
-            ok = poll_value<C>(t.ptag + ((trow * t.maxseg + s) * 64 + tid) * W, tag, &v, t.sync, t.status);
-            psum += v;
-          }
+          for (int sg = 0; sg < e.nseg - 1 && ok; ++sg)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+              C v = (C)0;
+              if (ok) ok = poll_value<C>(pwords(sg, q), tag, &v, t.sync, t.status);
+              psum[q] += v;
+            }
         // the words were loaded one tile earlier; poll only if they were not yet published
-        C v = (C)0;
-        if (ok && !Tagged<C>::check(pre, tag, &v)) ok = poll_value<C>(ywords(l), tag, &v, t.sync, t.status);
-        yb[l & 1][tid] = v;
-        if (l + 1 < e.nq) pre = Tagged<C>::load(ywords(l + 1));
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          C v = (C)0;
+          if (ok && !Tagged<C>::check(pre[q], tag, &v)) ok = poll_value<C>(ywords(l, q), tag, &v, t.sync, t.status);
+          yb[l & 1][q][tid] = v;
+        }
+        if (l + 1 < e.nq)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) pre[q] = Tagged<C>::load(ywords(l + 1, q));
       }
       if (!__syncthreads_and(ok)) {
         bad = true;
@@ -264,26 +281,35 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
       }
       if (tid == 0) pump();            // every thread is past tile l-1: its stage is free
       const S* tile = (const S*)(smem + (size_t)(cc % NSTAGE) * STAGE);
-      const C* y = yb[l & 1];
 #pragma unroll 8
-      for (int c = 32 * half; c < 32 * half + 32; ++c)
-        acc += (C)cvt(tile[Layout<S>::off(r, c)]) * y[c];
+      for (int c = 32 * half; c < 32 * half + 32; ++c) {
+        const C a = (C)cvt(tile[Layout<S>::off(r, c)]);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += a * yb[l & 1][q][c];
+      }
       cc++;
     }
     if (bad) break;
     if (!e.diag) {
-      red[tid] = acc;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) red[q][tid] = acc[q];
       __syncthreads();
       if (tid < 64)
-        Tagged<C>::put(t.ptag + ((trow * t.maxseg + e.seg) * 64 + tid) * W, red[tid] + red[tid + 64], tag);
+#pragma unroll
+        for (int q = 0; q < NR; ++q) Tagged<C>::put(pwords(e.seg, q), red[q][tid] + red[q][tid + 64], tag);
     } else {
       // diagonal block through its inverse: x = Inv (b - off-diagonal products)
-      red[tid] = acc;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) red[q][tid] = acc[q];
       bool ok = true;
-      if (e.nq == 0 && tid < 64)        // no own tile (first row of a sweep): no partials
-        psum = (C)0;
-      C own = rhs;
-      if (e.bwd && tid < 64) ok = poll_value<C>(t.ytag + (ro + tid) * W, tag_f, &own, t.sync, t.status);
+      C own[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        if (e.nq == 0) psum[q] = (C)0;  // no own tile (first row of a sweep): no partials
+        own[q] = rhs[q];
+        if (e.bwd && tid < 64 && ok)
+          ok = poll_value<C>(t.ytag + ((ro + tid) * NR + q) * W, tag_f, &own[q], t.sync, t.status);
+      }
       int staged = 0;
       for (int k = 0; k < PIECES && ok; ++k) {
         const bool sk = stage_ready(cc + k);
@@ -295,23 +321,31 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
         if (tid == 0) cc += staged;
         break;
       }
-      if (tid < 64) xb[tid] = own - ((red[tid] + red[tid + 64]) + psum);
+      if (tid < 64)
+#pragma unroll
+        for (int q = 0; q < NR; ++q) xb[q][tid] = own[q] - ((red[q][tid] + red[q][tid + 64]) + psum[q]);
       __syncthreads();
-      C part = (C)0;
+      C part[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) part[q] = (C)0;
 #pragma unroll 8
       for (int c = 32 * half; c < 32 * half + 32; ++c) {
         const int el = c * 64 + r;                      // column-major inverse element
         const C* piece = (const C*)(smem + (size_t)((cc + el / CPS) % NSTAGE) * STAGE);
-        part += piece[el % CPS] * xb[c];
+        const C a = piece[el % CPS];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) part[q] += a * xb[q][c];
       }
-      red2[tid] = part;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) red2[q][tid] = part[q];
       __syncthreads();
       if (tid < 64) {
-        const C x = red2[tid] + red2[tid + 64];
-        Tagged<C>::put(t.ytag + (ro + tid) * W, x, tag);
-        if (e.bwd) {
-          const int s = t.scatter[ro + tid];
-          if (s >= 0) zout[s] = (double)x;
+        const int sidx = e.bwd ? t.scatter[ro + tid] : -1;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const C x = red2[q][tid] + red2[q][tid + 64];
+          Tagged<C>::put(t.ytag + ((ro + tid) * NR + q) * W, x, tag);
+          if (sidx >= 0) z_out.ptr(q)[sidx] = (double)x;
         }
       }
       cc += PIECES;
@@ -394,27 +428,44 @@ int trsv_ctas_per_sm(int precision) {
   return precision == 0 ? 1 : (precision == 1 ? 3 : 6);
 }
 
+template <typename S, typename C, int NR> static cudaError_t prepare_nr() {
+  return cudaFuncSetAttribute(trsv_kernel<S, C, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)ring_bytes<S, C>());
+}
+template <typename S, typename C> static cudaError_t prepare_all() {
+  cudaError_t e = prepare_nr<S, C, 1>();
+  if (e == cudaSuccess) e = prepare_nr<S, C, 2>();
+  if (e == cudaSuccess) e = prepare_nr<S, C, 4>();
+  if (e == cudaSuccess) e = prepare_nr<S, C, 8>();
+  return e;
+}
+
 cudaError_t trsv_prepare(int precision) {
-  if (precision == 0)
-    return cudaFuncSetAttribute(trsv_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ring_bytes<double, double>());
-  if (precision == 1)
-    return cudaFuncSetAttribute(trsv_kernel<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)ring_bytes<float, float>());
-  return cudaFuncSetAttribute(trsv_kernel<__nv_bfloat16, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)ring_bytes<__nv_bfloat16, float>());
+  if (precision == 0) return prepare_all<double, double>();
+  if (precision == 1) return prepare_all<float, float>();
+  return prepare_all<__nv_bfloat16, float>();
+}
+
+template <typename S, typename C>
+static cudaError_t launch_typed(const TrsvDev& t, IndirectVec r_in, IndirectVec z_out, const int* done, int nr,
+                                cudaStream_t s) {
+  const size_t smem = ring_bytes<S, C>();
+  switch (nr) {
+    case 1: trsv_kernel<S, C, 1><<<t.grid, TRSV_THREADS, smem, s>>>(t, r_in, z_out, done); break;
+    case 2: trsv_kernel<S, C, 2><<<t.grid, TRSV_THREADS, smem, s>>>(t, r_in, z_out, done); break;
+    case 4: trsv_kernel<S, C, 4><<<t.grid, TRSV_THREADS, smem, s>>>(t, r_in, z_out, done); break;
+    case 8: trsv_kernel<S, C, 8><<<t.grid, TRSV_THREADS, smem, s>>>(t, r_in, z_out, done); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trsv(const TrsvDev& t, IndirectVec r_in, IndirectVec z_out, const int* done,
-                        cudaStream_t s) {
-  if (t.precision == 0)
-    trsv_kernel<double, double><<<t.grid, TRSV_THREADS, ring_bytes<double, double>(), s>>>(t, r_in, z_out, done);
-  else if (t.precision == 1)
-    trsv_kernel<float, float><<<t.grid, TRSV_THREADS, ring_bytes<float, float>(), s>>>(t, r_in, z_out, done);
-  else
-    trsv_kernel<__nv_bfloat16, float>
-        <<<t.grid, TRSV_THREADS, ring_bytes<__nv_bfloat16, float>(), s>>>(t, r_in, z_out, done);
-  return cudaGetLastError();
+                        cudaStream_t s, int nr) {
+  if (nr > t.nr_cap) return cudaErrorInvalidValue;
+  if (t.precision == 0) return launch_typed<double, double>(t, r_in, z_out, done, nr, s);
+  if (t.precision == 1) return launch_typed<float, float>(t, r_in, z_out, done, nr, s);
+  return launch_typed<__nv_bfloat16, float>(t, r_in, z_out, done, nr, s);
 }
 
 }  // namespace cpmdev
