@@ -14,7 +14,7 @@
 // position they wait for.
 //
 // Streaming.  Each CTA holds its current item and the next one; thread 0 keeps a ring of
-// NSTAGE shared-memory stages filled with 1-D bulk copies (TMA engine) across the item
+// ring_stages shared-memory stages filled with 1-D bulk copies (TMA engine) across the item
 // boundary, so the next item's tiles are already arriving while the current item waits
 // for its last dependency.  Solved pieces and partial sums are published as 64-bit words
 // that carry the launch epoch as a tag next to the value: consumers poll the data itself.
@@ -31,7 +31,10 @@
 namespace cpmdev {
 
 constexpr int TRSV_THREADS = 128;
-constexpr int NSTAGE = 4;
+// Stages of the shared-memory ring per CTA: 4 tiles (64 KB FP32, 32 KB BF16); FP64 tiles
+// are 32 KB, so 2 stages keep three CTAs per SM (another CTA's arithmetic overlaps a CTA's
+// waits, which matters where the FP64 pipe, not HBM, is the bound).
+template <typename S> __host__ __device__ constexpr int ring_stages() { return sizeof(S) == 8 ? 2 : 4; }
 constexpr int SEG_DIAG = 0x3ff;
 
 __device__ __forceinline__ double cvt(double v) { return v; }
@@ -136,6 +139,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   constexpr int PIECES = (int)(sizeof(C) / sizeof(S));        // stages per inverse tile
   constexpr int W = Tagged<C>::WORDS;
   constexpr int CPS = STAGE / sizeof(C);                      // C values per stage
+  constexpr int NSTAGE = ring_stages<S>();
   static_assert(PIECES >= 1 && PIECES <= 2 && NSTAGE >= PIECES, "ring too small");
   __shared__ __align__(8) uint64_t bar[NSTAGE];
   __shared__ C yb[2][NR][64];                                 // solved pieces, double-buffered
@@ -281,12 +285,22 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
       }
       if (tid == 0) pump();            // every thread is past tile l-1: its stage is free
       const S* tile = (const S*)(smem + (size_t)(cc % NSTAGE) * STAGE);
-#pragma unroll 8
-      for (int c = 32 * half; c < 32 * half + 32; ++c) {
-        const C a = (C)cvt(tile[Layout<S>::off(r, c)]);
+      // four independent partial sums per right-hand side (hides the FMA latency)
+      C a4[NR][4];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] += a * yb[l & 1][q][c];
-      }
+      for (int q = 0; q < NR; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a4[q][u] = (C)0;
+#pragma unroll
+      for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 4)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const C a = (C)cvt(tile[Layout<S>::off(r, c0 + u)]);
+#pragma unroll
+          for (int q = 0; q < NR; ++q) a4[q][u] += a * yb[l & 1][q][c0 + u];
+        }
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] += (a4[q][0] + a4[q][1]) + (a4[q][2] + a4[q][3]);
       cc++;
     }
     if (bad) break;
@@ -325,19 +339,23 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
 #pragma unroll
         for (int q = 0; q < NR; ++q) xb[q][tid] = own[q] - ((red[q][tid] + red[q][tid + 64]) + psum[q]);
       __syncthreads();
-      C part[NR];
+      C p4[NR][4];
 #pragma unroll
-      for (int q = 0; q < NR; ++q) part[q] = (C)0;
-#pragma unroll 8
-      for (int c = 32 * half; c < 32 * half + 32; ++c) {
-        const int el = c * 64 + r;                      // column-major inverse element
-        const C* piece = (const C*)(smem + (size_t)((cc + el / CPS) % NSTAGE) * STAGE);
-        const C a = piece[el % CPS];
+      for (int q = 0; q < NR; ++q)
 #pragma unroll
-        for (int q = 0; q < NR; ++q) part[q] += a * xb[q][c];
-      }
+        for (int u = 0; u < 4; ++u) p4[q][u] = (C)0;
 #pragma unroll
-      for (int q = 0; q < NR; ++q) red2[q][tid] = part[q];
+      for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 4)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int el = (c0 + u) * 64 + r;               // column-major inverse element
+          const C* piece = (const C*)(smem + (size_t)((cc + el / CPS) % NSTAGE) * STAGE);
+          const C a = piece[el % CPS];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) p4[q][u] += a * xb[q][c0 + u];
+        }
+#pragma unroll
+      for (int q = 0; q < NR; ++q) red2[q][tid] = (p4[q][0] + p4[q][1]) + (p4[q][2] + p4[q][3]);
       __syncthreads();
       if (tid < 64) {
         const int sidx = e.bwd ? t.scatter[ro + tid] : -1;
@@ -421,11 +439,11 @@ void trsv_build_items(const int* T, int n_sub, int kseg, int stagger, std::vecto
   *maxseg = ms;
 }
 
-template <typename S, typename C> constexpr size_t ring_bytes() { return NSTAGE * sizeof(S) * TILE_ELEMS; }
+template <typename S, typename C> constexpr size_t ring_bytes() { return ring_stages<S>() * sizeof(S) * TILE_ELEMS; }
 
 int trsv_ctas_per_sm(int precision) {
-  // 4-stage ring: fp64 128 KB, fp32 64 KB, bf16 32 KB of shared memory per CTA
-  return precision == 0 ? 1 : (precision == 1 ? 3 : 6);
+  // rings: fp64 2 x 32 KB, fp32 4 x 16 KB, bf16 4 x 8 KB of shared memory per CTA
+  return precision == 0 ? 3 : (precision == 1 ? 3 : 6);
 }
 
 template <typename S, typename C, int NR> static cudaError_t prepare_nr() {
