@@ -126,14 +126,27 @@ __global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(T* a, const Sub
 
 // ---------------------------------------------------------------- panel in a cluster
 // The same panel factorisation with the panel held in shared memory: a cluster of CS CTAs
-// per subdomain, CTA r holding rows [k0 + r R, k0 + (r+1) R) of the panel's 64 columns.  Per
-// column: every CTA reduces its candidate (max |a|, lowest row on ties) -> cluster barrier ->
-// every CTA reads the CS candidates and the pivot row through distributed shared memory (the
-// pivot CTA also reads the row it swaps with) -> cluster barrier -> the two owners write the
-// swapped rows, every CTA updates its rows below the pivot and reduces the next column's
-// candidate in the same pass.  Same arithmetic, element by element, as lu_panel_kernel.
+// per subdomain, CTA r holding rows [k0 + r R, k0 + (r+1) R) of the panel's 64 columns.
+// Rows are not moved during the panel: every row carries its logical position (the row index
+// it would have after the interchanges so far).  Per column: cluster barrier -> every CTA
+// reads the CS candidates (max |a|, lowest logical row on ties) and then the pivot row in
+// place through distributed shared memory (a finished pivot row never changes again) ->
+// every CTA relabels the pivot row and the row it displaces, updates its rows below the
+// pivot and reduces the next column's candidate in the same pass.  One cluster barrier per
+// column; the rows are written back to their final positions at the end.  Same pivots and
+// the same arithmetic, element by element, as lu_panel_kernel.
 constexpr int PC_THREADS = 256;
-constexpr int PC_STRIDE = 65;                 // panel row stride (elements)
+// Panel rows are 16-byte aligned (68 floats / 66 doubles: 128-bit accesses of a quarter warp
+// to consecutive rows fall in distinct bank groups) and updated 16 bytes at a time.
+template <typename T> struct PanelVec;
+template <> struct PanelVec<float> {
+  using V = float4;
+  static constexpr int N = 4, STRIDE = 68;
+};
+template <> struct PanelVec<double> {
+  using V = double2;
+  static constexpr int N = 2, STRIDE = 66;
+};
 constexpr int PC_SMEM = 200 * 1024;           // dynamic shared memory for panel rows
 
 __device__ __forceinline__ void argmax_pair(double& v, int& i, double ov, int oi) {
@@ -161,6 +174,9 @@ template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) lu_panel_cluster_kernel(T* a, const SubMeta* __restrict__ meta,
                                                                       int32_t* ipiv, int* status, int s,
                                                                       int rows_per_cta) {
+  constexpr int PC_STRIDE = PanelVec<T>::STRIDE;
+  constexpr int VN = PanelVec<T>::N;
+  using VT = typename PanelVec<T>::V;
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -168,10 +184,13 @@ __global__ void __launch_bounds__(PC_THREADS) lu_panel_cluster_kernel(T* a, cons
   if (s >= m.T) return;                         // the whole cluster (one subdomain) leaves together
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* panel = (T*)smem_raw;
+  // logical row (index within the subdomain) of every physical slot; rows with a logical
+  // index below the current column are finished pivot rows and never change again
+  int* lg = (int*)(smem_raw + (size_t)rows_per_cta * PC_STRIDE * sizeof(T));
   __shared__ double cval[2], wv[PC_THREADS / 32];
-  __shared__ int cidx[2], wi[PC_THREADS / 32];
-  __shared__ T prow[64], trow[64];
-  __shared__ int piv_sh;
+  __shared__ int cidx[2], cloc[2], wi[PC_THREADS / 32], wl[PC_THREADS / 32];
+  __shared__ __align__(16) T prow[64];
+  __shared__ int piv_sh, piv_rank, piv_slot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k0 = 64 * s, np = 64 * m.T;
   const int r0 = k0 + rank * rows_per_cta;
@@ -180,79 +199,118 @@ __global__ void __launch_bounds__(PC_THREADS) lu_panel_cluster_kernel(T* a, cons
     const int i = e % nr, j = e / nr;
     panel[i * PC_STRIDE + j] = at(a, m, r0 + i, k0 + j);
   }
+  for (int i = tid; i < nr; i += PC_THREADS) lg[i] = r0 + i;
+  // block candidate (max |value|, lowest logical row on ties) with its slot -> slot sl
+  auto block_candidate = [&](double best, int bi, int bs, int sl) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o), os = __shfl_xor_sync(0xffffffffu, bs, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; bs = os; }
+    }
+    if (lane == 0) { wv[warp] = best; wi[warp] = bi; wl[warp] = bs; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = wv[0];
+      int i = wi[0], l = wl[0];
+      for (int w = 1; w < PC_THREADS / 32; ++w)
+        if (wv[w] > b || (wv[w] == b && wi[w] < i)) { b = wv[w]; i = wi[w]; l = wl[w]; }
+      cval[sl] = b;
+      cidx[sl] = i;
+      cloc[sl] = l;
+    }
+  };
   __syncthreads();
   {
     double best = -1.0;
-    int bi = 0x7fffffff;
+    int bi = 0x7fffffff, bs = -1;
     for (int i = tid; i < nr; i += PC_THREADS) {
       const double v = fabs((double)panel[i * PC_STRIDE]);
-      if (v > best) { best = v; bi = r0 + i; }
+      if (v > best) { best = v; bi = r0 + i; bs = i; }
     }
-    block_argmax(best, bi, wv, wi, &cval[0], &cidx[0]);
+    block_candidate(best, bi, bs, 0);
   }
   for (int c = 0; c < 64; ++c) {
     const int col = k0 + c, slot = c & 1;
-    cl.sync();                                  // candidates of column c are visible
+    cl.sync();                                  // every CTA's candidate of column c is visible
     if (warp == 0) {
       double v = -1.0;
-      int ix = 0x7fffffff;
+      int ix = 0x7fffffff, loc = -1, rk = -1;
       if (lane < cs) {
         v = *cl.map_shared_rank(&cval[slot], lane);
         ix = *cl.map_shared_rank(&cidx[slot], lane);
+        loc = *cl.map_shared_rank(&cloc[slot], lane);
+        rk = lane;
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-        argmax_pair(v, ix, __shfl_xor_sync(0xffffffffu, v, o), __shfl_xor_sync(0xffffffffu, ix, o));
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ix, o), ol = __shfl_xor_sync(0xffffffffu, loc, o);
+        const int orr = __shfl_xor_sync(0xffffffffu, rk, o);
+        if (ov > v || (ov == v && oi < ix)) { v = ov; ix = oi; loc = ol; rk = orr; }
+      }
       if (lane == 0) {
-        if (!(v > 0.0)) {                       // zero (or NaN) column: singular local matrix
+        if (!(v > 0.0) || loc < 0) {            // zero (or NaN) column: singular local matrix
           if (rank == 0) atomicOr(status, ST_SINGULAR);
-          ix = col;
+          ix = -1;
         }
         piv_sh = ix;
+        piv_rank = rk;
+        piv_slot = loc;
       }
     }
     __syncthreads();
-    const int p = piv_sh;
-    const int oc = (col - k0) / rows_per_cta, op = (p - k0) / rows_per_cta;
-    if (tid < 64) {
-      prow[tid] = cl.map_shared_rank(panel, op)[(p - (k0 + op * rows_per_cta)) * PC_STRIDE + tid];
-      if (rank == op && p != col)
-        trow[tid] = cl.map_shared_rank(panel, oc)[(col - (k0 + oc * rows_per_cta)) * PC_STRIDE + tid];
-    }
-    cl.sync();                                  // rows col and p have been read everywhere
-    if (p != col && tid < 64) {
-      if (rank == oc) panel[(col - r0) * PC_STRIDE + tid] = prow[tid];
-      if (rank == op) panel[(p - r0) * PC_STRIDE + tid] = trow[tid];
-    }
-    if (rank == 0 && tid == 0) ipiv[m.row_off + col] = p;
+    const int p = piv_sh;                       // logical row chosen (-1: singular column)
+    const int prk = piv_rank, psl = piv_slot;
+    if (tid < 64) prow[tid] = p >= 0 ? cl.map_shared_rank(panel, prk)[psl * PC_STRIDE + tid] : (T)0;
+    if (rank == 0 && tid == 0) ipiv[m.row_off + col] = p >= 0 ? p : col;
     __syncthreads();
     const T d = prow[c];
     const T inv = d != (T)0 ? (T)1 / d : (T)0;
     double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int i = max(0, col + 1 - r0) + tid; i < nr; i += PC_THREADS) {
+    int bi = 0x7fffffff, bs = -1;
+    for (int i = tid; i < nr; i += PC_THREADS) {
+      int L = lg[i];
+      if (L < col) continue;                     // finished pivot row
+      if (p >= 0) {
+        if (rank == prk && i == psl) { lg[i] = col; continue; }   // the pivot row: logical col
+        if (L == col) { L = p; lg[i] = p; }      // the row displaced from position col
+      } else if (L == col) {
+        continue;                                // singular column: the row at col stays
+      }
       T* row = panel + i * PC_STRIDE;
       const T l = row[c] * inv;
       row[c] = l;
-      for (int cc = c + 1; cc < 64; ++cc) row[cc] -= l * prow[cc];
+      // columns c+1 .. 63, VN at a time from the group holding column c+1
+      for (int g = (c + 1) / VN; g < 64 / VN; ++g) {
+        VT v = ((VT*)row)[g];
+        const VT pv = ((const VT*)prow)[g];
+        T* ve = (T*)&v;
+        const T* pe = (const T*)&pv;
+#pragma unroll
+        for (int u = 0; u < VN; ++u)
+          if (VN * g + u > c) ve[u] -= l * pe[u];
+        ((VT*)row)[g] = v;
+      }
       if (c + 1 < 64) {
         const double v = fabs((double)row[c + 1]);
-        if (v > best) { best = v; bi = r0 + i; }
+        if (v > best || (v == best && L < bi)) { best = v; bi = L; bs = i; }
       }
     }
-    if (c + 1 < 64) block_argmax(best, bi, wv, wi, &cval[slot ^ 1], &cidx[slot ^ 1]);
+    if (c + 1 < 64) block_candidate(best, bi, bs, slot ^ 1);
   }
   __syncthreads();
   for (int e = tid; e < nr * 64; e += PC_THREADS) {
     const int i = e % nr, j = e / nr;
-    at(a, m, r0 + i, k0 + j) = panel[i * PC_STRIDE + j];
+    at(a, m, lg[i], k0 + j) = panel[i * PC_STRIDE + j];
   }
   cl.sync();                                    // no CTA leaves while its panel may be read
 }
 
 // Cluster size and rows per CTA for a panel of at most max_rows rows; 0 if it does not fit.
 static int panel_cluster_size(int max_rows, size_t elem, int* rows_per_cta) {
-  const int cap = PC_SMEM / (PC_STRIDE * (int)elem);
+  const int stride = elem == 8 ? PanelVec<double>::STRIDE : PanelVec<float>::STRIDE;
+  const int cap = PC_SMEM / (stride * (int)elem + (int)sizeof(int));
   for (int cs = 1; cs <= 16; cs *= 2) {
     const int r = (max_rows + cs - 1) / cs;
     if (r <= cap) {
@@ -268,7 +326,7 @@ static cudaError_t launch_panel_cluster(const FactorDev& f, int step, int cs, in
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(f.n_sub * cs);
   cfg.blockDim = dim3(PC_THREADS);
-  cfg.dynamicSmemBytes = (size_t)rpc * PC_STRIDE * sizeof(T);
+  cfg.dynamicSmemBytes = (size_t)rpc * PanelVec<T>::STRIDE * sizeof(T) + (size_t)rpc * sizeof(int);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
