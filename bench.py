@@ -41,6 +41,20 @@ def _dist():
     return world, rank, local
 
 
+def replica_rate(total_ms: float, steps: int, device=None):
+    """Replicas (one independent solver per GPU, no collective on the data path): the job's
+    timed region is the slowest rank's, the rate counts every rank's solves.  Returns
+    (max total ms over ranks, whole-job solves/s)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps / (total_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -226,15 +240,10 @@ def run_native(args):
     if world > 1:
         torch.distributed.barrier()
     per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = sum(per_step)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms, value = replica_rate(sum(per_step), args.steps, dev)
     launches = pc.info()["kernel_launches"] - launches0
     iters = results[-1][0]["iterations"]
     relres = results[-1][0]["relres"]
-    value = world * args.steps / (total_ms / 1e3)
 
     # ---- solution error of the mixed path against the FP64 path ----
     extra = {}
