@@ -343,7 +343,14 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   FactorDev f{work, pc->d_meta, ipiv, pc->status, ns, t_max, fp64 ? 1 : 0};
   // FP32: split-tf32 tensor-core update (FP32 accuracy); BF16: bf16 inputs, FP32 accumulate
   const int use_tc = (precision == CPM_FP64 || simt_lu) ? 0 : (precision == CPM_BF16 ? 2 : 1);
-  if (use_tc) CK(lu_tc_prepare());
+  void* ubuf = nullptr;
+  if (use_tc) {
+    CK(lu_tc_prepare());
+    cudaError_t e;
+    ubuf = pc->alloc(lu_tc_ubuf_bytes(row_off / TILE, use_tc == 2), &e);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc split U operands");
+    f.ubuf = ubuf;
+  }
   CK(lu_panel_prepare());
   for (int step = 0; step < t_max; ++step) CK(launch_lu_step(f, step, use_tc, s));
   CK(launch_lu_finish(f, d_unk, d_unk_off, d_own, pc->gather, pc->scatter, dinv, s));
@@ -370,6 +377,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   pc->release(d_own);
   pc->release(d_unk_off);
   pc->release(ipiv);
+  if (ubuf) pc->release(ubuf);
   int hst = 0;
   CK(cudaMemcpy(&hst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (hst & ST_SINGULAR) {
@@ -767,7 +775,8 @@ cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmissio
   const int64_t gmres = rnd(8 * (restart + 1) * N) + rnd(8 * restart * N) + 2 * rnd(8 * N) +
                         rnd(8 * nblk * (restart + 2)) + rnd(8 * (int64_t)(restart + 2) * (restart + 8) + 4096) +
                         rnd(64) + rnd(8 * NN) /* extension values */ + rnd(8 * nrhs * NN) /* apply scratch */;
-  const int64_t setup_peak = band_dev + work + inv + small + assembly +
+  const int64_t ubuf = precision == CPM_FP64 ? 0 : rnd((int64_t)lu_tc_ubuf_bytes(rows / TILE, precision == CPM_BF16));
+  const int64_t setup_peak = band_dev + work + inv + small + assembly + ubuf +
                              (precision == CPM_BF16 ? rnd(2 * tile_elems) : 0);
   const int64_t resident = band_dev + rnd(factor) + inv + small + sched + gmres;
   out->setup_peak_bytes = setup_peak + (setup_peak >> 6);

@@ -70,6 +70,8 @@ struct FactorDev {
   int n_sub;
   int t_max;
   int fp64;                // 1: double tiles, 0: float (swizzled) tiles
+  void* ubuf = nullptr;    // tensor-core update: the step's U row split into MMA operands
+                           // (lu_tc_ubuf_bytes(rows_total / 64, bf16) bytes)
 };
 cudaError_t launch_scatter(void* a, int fp64, const int64_t* off, const double* val, int64_t nnz,
                            cudaStream_t s);
@@ -80,6 +82,7 @@ cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_
 // jchunk: tile columns per CTA (0 = default)
 cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s, int jchunk = 0);
 cudaError_t lu_tc_prepare();
+size_t lu_tc_ubuf_bytes(int64_t tile_rows_total, int bf16);
 // Panel factorisation in a thread-block cluster (shared-memory panel); call once per device
 // before launch_lu_step.  Without it the panel runs on one CTA per subdomain from global memory.
 cudaError_t lu_panel_prepare();

@@ -136,18 +136,52 @@ __device__ __forceinline__ uint32_t bf16_b_off(int k, int n) {
 constexpr int TC_JCHUNK = 32;           // tile columns per CTA (default of launch_lu_update_tc)
 template <int KIND> struct TcSmem;
 template <> struct TcSmem<2> {    // A hi / lo 64 KB, B stages 2 x (hi 16 + lo 16 KB), C stages 2 x 32 KB
-  static constexpr uint32_t A_HI = 0, A_LO = 32768, B0 = 65536, BSTAGE = 32768, C0 = 131072, CSTAGE = 32768,
-                            A_RAW = C0 + CSTAGE, TOTAL = 196608;
+  static constexpr uint32_t A_HI = 0, A_LO = 32768, B0 = 65536, BSTAGE = 32768, BBYTES = 32768, C0 = 131072,
+                            CSTAGE = 32768, A_RAW = C0 + CSTAGE, TOTAL = 196608;
 };
-template <> struct TcSmem<1> {    // A bf16 16 KB, B stages 2 x (raw 16 + bf16 8 KB), C stages 2 x 32 KB
-  static constexpr uint32_t A_BF = 0, B0 = 16384, BSTAGE = 24576, C0 = 65536, CSTAGE = 32768,
-                            A_RAW = C0 + CSTAGE, TOTAL = 131072;
+template <> struct TcSmem<1> {    // A bf16 16 KB, B stages 2 x bf16 8 KB, C stages 2 x 32 KB
+  static constexpr uint32_t A_BF = 0, B0 = 16384, BSTAGE = 8192, BBYTES = 8192, C0 = 32768, CSTAGE = 32768,
+                            A_RAW = C0 + CSTAGE, TOTAL = 98304;
 };
 // (the raw A pair is staged in C stage 1, which is refilled once A has been converted)
 
+// The U row of step s, split once per step into the B-operand form the MMAs read (tf32 hi
+// then lo, 16 KB each, in the tile's own K-major layout; or bf16, 8 KB, K-major): slot
+// row_off/64 + J of the buffer holds tile (s, J) of that subdomain.
+template <int KIND>
+__global__ void __launch_bounds__(256) lu_split_u_kernel(const float* __restrict__ a, const SubMeta* __restrict__ meta,
+                                                         int s, unsigned char* __restrict__ ubuf) {
+  const SubMeta m = meta[blockIdx.y];
+  const int J = s + 1 + blockIdx.x;
+  if (J >= m.T) return;
+  const float* t = a + tile_base(m, s, J);
+  unsigned char* dst = ubuf + (size_t)((m.row_off >> 6) + J) * TcSmem<KIND>::BBYTES;
+  if (KIND == 2) {
+    const float4* src4 = (const float4*)t;
+    float4* hi4 = (float4*)dst;
+    float4* lo4 = (float4*)(dst + 16384);
+    for (int e = threadIdx.x; e < TILE_ELEMS / 4; e += 256) {
+      const float4 x = src4[e];
+      float4 hi, lo;
+      hi.x = tf32_round(x.x); lo.x = tf32_round(x.x - hi.x);
+      hi.y = tf32_round(x.y); lo.y = tf32_round(x.y - hi.y);
+      hi.z = tf32_round(x.z); lo.z = tf32_round(x.z - hi.z);
+      hi.w = tf32_round(x.w); lo.w = tf32_round(x.w - hi.w);
+      hi4[e] = hi;
+      lo4[e] = lo;
+    }
+  } else {
+    for (int e = threadIdx.x; e < TILE_ELEMS; e += 256) {
+      const int k = e & 63, n = e >> 6;
+      *(__nv_bfloat16*)(dst + bf16_b_off(k, n)) = __float2bfloat16_rn(t[off_sw32(k, n)]);
+    }
+  }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, const SubMeta* __restrict__ meta,
-                                                                   int s, int jchunk, int* status) {
+                                                                   const unsigned char* __restrict__ ubuf, int s,
+                                                                   int jchunk, int* status) {
   using L = TcSmem<KIND>;
   const SubMeta m = meta[blockIdx.z];
   const int I0 = s + 1 + 2 * blockIdx.x, I1 = I0 + 1;
@@ -183,8 +217,8 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
   auto stage_b = [&](int b) { return (float*)(base + L::B0 + b * L::BSTAGE); };
   auto stage_c = [&](int b) { return (float*)(base + L::C0 + b * L::CSTAGE); };
   auto issue_b = [&](int b, int J) {
-    mbar_expect_tx(&bar_b[b], 16384u);
-    bulk_g2s(stage_b(b), a + tile_base(m, s, J), 16384, &bar_b[b]);
+    mbar_expect_tx(&bar_b[b], L::BBYTES);
+    bulk_g2s(stage_b(b), ubuf + (size_t)((m.row_off >> 6) + J) * L::BBYTES, L::BBYTES, &bar_b[b]);
     nb_iss[b]++;
   };
   auto issue_c = [&](int b, int J) {
@@ -240,49 +274,24 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
   int v_line[8];                                // in-atom offset of column line l of this row
 #pragma unroll
   for (int l = 0; l < 8; ++l) v_line[l] = (l << 5) + ((((lr >> 2) & 7) ^ l) << 2);
-  // software pipeline: iteration it converts U tile J = Jbeg + it and issues its MMAs into
-  // accumulator buffer it & 1, then finishes column J - 1 (epilogue from buffer (it-1) & 1)
+  // software pipeline: in iteration it thread 0 issues the MMAs of U tile J = Jbeg + it into
+  // accumulator buffer it & 1 as soon as that tile lands (a failed wait there is broadcast by
+  // the barrier of the next iteration), then all threads finish column J - 1 (epilogue from
+  // buffer (it-1) & 1)
   for (int it = 0; ok && it <= nJ; ++it) {
-    if (it < nJ) {
+    if (it < nJ && tid == 0 && sh_ok) {
+      // thread 0 alone: the pre-split U tile lands in stage b, the MMAs go into buffer b
       const int b = it & 1;
       const uint32_t ph = (uint32_t)(it >> 1) & 1;
-      if (tid == 0) {
-        sh_ok = mbar_wait_bounded(&bar_b[b], ph) ? 1 : 0;
-        if (!sh_ok) atomicOr(status, ST_TIMEOUT);
-        else nb_wait[b]++;
-      }
-      __syncthreads();
-      if (!sh_ok) { ok = false; break; }
-      mbar_wait_bounded(&bar_b[b], ph);
-      float* rb = stage_b(b);
-      if (KIND == 2) {                          // B_hi in place, B_lo in the second half
-        float4* b4 = (float4*)rb;
-        float4* l4 = (float4*)(rb + TILE_ELEMS);
-#pragma unroll
-        for (int e = tid; e < TILE_ELEMS / 4; e += TC_THREADS) {
-          const float4 x = b4[e];
-          float4 hi, lo;
-          hi.x = tf32_round(x.x); lo.x = tf32_round(x.x - hi.x);
-          hi.y = tf32_round(x.y); lo.y = tf32_round(x.y - hi.y);
-          hi.z = tf32_round(x.z); lo.z = tf32_round(x.z - hi.z);
-          hi.w = tf32_round(x.w); lo.w = tf32_round(x.w - hi.w);
-          b4[e] = hi;
-          l4[e] = lo;
-        }
+      if (!mbar_wait_bounded(&bar_b[b], ph)) {
+        atomicOr(status, ST_TIMEOUT);
+        sh_ok = 0;
       } else {
-        unsigned char* bbf = (unsigned char*)(rb + TILE_ELEMS);
-        for (int e = tid; e < TILE_ELEMS; e += TC_THREADS) {
-          const int k = e & 63, n = e >> 6;
-          *(__nv_bfloat16*)(bbf + bf16_b_off(k, n)) = __float2bfloat16_rn(rb[off_sw32(k, n)]);
-        }
-      }
-      fence_proxy_async();                      // generic-proxy writes -> tensor-core reads
-      __syncthreads();
-      if (tid == 0) {
+        nb_wait[b]++;
         fence_after_sync();
         const uint32_t d_tmem = taddr + (uint32_t)(b * TC_TMEM_COLS);
         // a descriptor's start-address field holds addr >> 4: an offset adds (off >> 4)
-        const uint64_t db = smem_desc(smem_u32(rb), 16, 1024);
+        const uint64_t db = smem_desc(smem_u32(stage_b(b)), 16, 1024);
         if (KIND == 2) {
           constexpr uint32_t idesc = instr_desc(2);
           const uint64_t dhi = smem_desc(smem_u32(base) + TcSmem<2>::A_HI, 16, 1024);
@@ -300,7 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
           const uint64_t da = smem_desc(smem_u32(base) + TcSmem<1>::A_BF, 16, 1024);
 #pragma unroll
           for (int k = 0; k < 4; ++k)           // K = 16 bf16 values (32 bytes) per instruction
-            mma<1>(d_tmem, da + ((k * 32) >> 4), db + ((16384 + k * 32) >> 4), idesc, k > 0 ? 1u : 0u);
+            mma<1>(d_tmem, da + ((k * 32) >> 4), db + ((k * 32) >> 4), idesc, k > 0 ? 1u : 0u);
         }
         mma_commit(&bar_mma[b]);
         nm_iss[b]++;
@@ -309,7 +318,7 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
     if (it > 0) {                               // finish column J - 1
       const int p = it - 1, bp = p & 1;
       const uint32_t php = (uint32_t)(p >> 1) & 1;
-      if (tid == 0) {
+      if (tid == 0 && sh_ok) {
         sh_ok = mbar_wait_bounded(&bar_mma[bp], php) ? 1 : 0;
         if (!sh_ok) atomicOr(status, ST_TIMEOUT);
         else nm_wait[bp]++;
@@ -374,13 +383,25 @@ cudaError_t lu_tc_prepare() {
 cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStream_t s, int jchunk) {
   const int W = f.t_max - 1 - step;
   if (W <= 0) return cudaSuccess;
+  if (!f.ubuf) return cudaErrorInvalidValue;
   if (jchunk < 1) jchunk = TC_JCHUNK;
+  dim3 gs(W, f.n_sub);
   dim3 g((W + 1) / 2, (W + jchunk - 1) / jchunk, f.n_sub);
-  if (bf16)
-    lu_update_tc_kernel<1><<<g, TC_THREADS, 1024 + TcSmem<1>::TOTAL, s>>>((float*)f.a, f.meta, step, jchunk, f.status);
-  else
-    lu_update_tc_kernel<2><<<g, TC_THREADS, 1024 + TcSmem<2>::TOTAL, s>>>((float*)f.a, f.meta, step, jchunk, f.status);
+  unsigned char* ub = (unsigned char*)f.ubuf;
+  if (bf16) {
+    lu_split_u_kernel<1><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub);
+    lu_update_tc_kernel<1><<<g, TC_THREADS, 1024 + TcSmem<1>::TOTAL, s>>>((float*)f.a, f.meta, ub, step, jchunk,
+                                                                          f.status);
+  } else {
+    lu_split_u_kernel<2><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub);
+    lu_update_tc_kernel<2><<<g, TC_THREADS, 1024 + TcSmem<2>::TOTAL, s>>>((float*)f.a, f.meta, ub, step, jchunk,
+                                                                          f.status);
+  }
   return cudaGetLastError();
+}
+
+size_t lu_tc_ubuf_bytes(int64_t tile_rows_total, int bf16) {
+  return (size_t)tile_rows_total * (bf16 ? TcSmem<1>::BBYTES : TcSmem<2>::BBYTES);
 }
 
 }  // namespace cpmdev
