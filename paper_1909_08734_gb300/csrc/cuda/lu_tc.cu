@@ -22,7 +22,9 @@
 
 namespace cpmdev {
 
-constexpr int TC_THREADS = 256;          // 8 warps: two per tensor-memory lane quarter
+// threads of the update kernel: 16 warps (four per tensor-memory lane quarter) for split tf32,
+// whose 194 KB of shared memory allows one CTA per SM; 8 warps for bf16 (two CTAs per SM)
+template <int KIND> __host__ __device__ constexpr int tc_threads() { return KIND == 2 ? 512 : 256; }
 constexpr int TC_TMEM_COLS = 64;         // FP32 accumulator columns per buffer (two buffers)
 
 // ---- tcgen05 / descriptor helpers -------------------------------------------------------
@@ -104,6 +106,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -137,11 +151,11 @@ constexpr int TC_JCHUNK = 32;           // tile columns per CTA (default of laun
 template <int KIND> struct TcSmem;
 template <> struct TcSmem<2> {    // A hi / lo 64 KB, B stages 2 x (hi 16 + lo 16 KB), C stages 2 x 32 KB
   static constexpr uint32_t A_HI = 0, A_LO = 32768, B0 = 65536, BSTAGE = 32768, BBYTES = 32768, C0 = 131072,
-                            CSTAGE = 32768, A_RAW = C0 + CSTAGE, TOTAL = 196608;
+                            CSTAGE = 32768, NC = 2, A_RAW = C0 + CSTAGE, TOTAL = C0 + NC * CSTAGE;
 };
-template <> struct TcSmem<1> {    // A bf16 16 KB, B stages 2 x bf16 8 KB, C stages 2 x 32 KB
+template <> struct TcSmem<1> {    // A bf16 16 KB, B stages 2 x bf16 8 KB, C stages 2 x 32 KB (2 CTAs per SM)
   static constexpr uint32_t A_BF = 0, B0 = 16384, BSTAGE = 8192, BBYTES = 8192, C0 = 32768, CSTAGE = 32768,
-                            A_RAW = C0 + CSTAGE, TOTAL = 98304;
+                            NC = 2, A_RAW = C0 + CSTAGE, TOTAL = C0 + NC * CSTAGE;
 };
 // (the raw A pair is staged in C stage 1, which is refilled once A has been converted)
 
@@ -179,10 +193,13 @@ __global__ void __launch_bounds__(256) lu_split_u_kernel(const float* __restrict
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, const SubMeta* __restrict__ meta,
+__global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float* a, const SubMeta* __restrict__ meta,
                                                                    const unsigned char* __restrict__ ubuf, int s,
                                                                    int jchunk, int* status) {
   using L = TcSmem<KIND>;
+  constexpr int TC_THREADS = tc_threads<KIND>();
+  constexpr int TC_CG = TC_THREADS / 128;      // epilogue column groups (warps per lane quarter)
+  constexpr int TC_CW = 64 / TC_CG;            // accumulator columns per warp in the epilogue
   const SubMeta m = meta[blockIdx.z];
   const int I0 = s + 1 + 2 * blockIdx.x, I1 = I0 + 1;
   const int Jbeg = s + 1 + blockIdx.y * jchunk;
@@ -192,21 +209,22 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
   const uint32_t pair_bytes = two ? 32768u : 16384u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bar_a, bar_b[2], bar_c[2], bar_mma[2];
+  constexpr int NC = (int)L::NC;               // C stages
+  __shared__ __align__(8) uint64_t bar_a, bar_b[2], bar_c[NC], bar_mma[2];
   __shared__ uint32_t tmem_slot;
   __shared__ int sh_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // copies and commits issued / waited per stage (thread 0), for the drain after an abort
-  int nb_iss[2] = {0, 0}, nb_wait[2] = {0, 0}, nc_iss[2] = {0, 0}, nc_wait[2] = {0, 0};
+  int nb_iss[2] = {0, 0}, nb_wait[2] = {0, 0}, nc_iss[NC] = {}, nc_wait[NC] = {};
   int nm_iss[2] = {0, 0}, nm_wait[2] = {0, 0};
   bool a_done = false;
   if (tid == 0) {
     mbar_init(&bar_a, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&bar_b[b], 1);
-      mbar_init(&bar_c[b], 1);
       mbar_init(&bar_mma[b], 1);
     }
+    for (int b = 0; b < NC; ++b) mbar_init(&bar_c[b], 1);
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(&tmem_slot, 2 * TC_TMEM_COLS);
@@ -233,6 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
     if (two) bulk_g2s(rawA + TILE_ELEMS, a + tile_base(m, I1, s), 16384, &bar_a);
     for (int b = 0; b < 2 && b < nJ; ++b) issue_b(b, Jbeg + b);
     issue_c(0, Jbeg);
+    for (int b = 2; b < NC && b < nJ; ++b) issue_c(b, Jbeg + b);   // stage 1 holds raw A for now
     sh_ok = mbar_wait_bounded(&bar_a, 0) ? 1 : 0;
     if (!sh_ok) atomicOr(status, ST_TIMEOUT);
     a_done = sh_ok;
@@ -267,8 +286,8 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
     if (tid == 0 && nJ > 1) issue_c(1, Jbeg + 1);
   }
   // epilogue assignment: warp w owns rows 32 (w & 3) + lane (tensor-memory lanes of its
-  // quarter) and columns 32 (w >> 2) .. + 31
-  const int row = 32 * (warp & 3) + lane, colh = warp >> 2;
+  // quarter) and columns TC_CW (w >> 2) .. + TC_CW - 1
+  const int row = 32 * (warp & 3) + lane, colg = warp >> 2;
   const bool mine = row < 64 || two;
   const int lr = row & 63;
   int v_line[8];                                // in-atom offset of column line l of this row
@@ -316,8 +335,8 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
       }
     }
     if (it > 0) {                               // finish column J - 1
-      const int p = it - 1, bp = p & 1;
-      const uint32_t php = (uint32_t)(p >> 1) & 1;
+      const int p = it - 1, bp = p & 1, cp = p % NC;
+      const uint32_t php = (uint32_t)(p >> 1) & 1, phc = (uint32_t)(p / NC) & 1;
       if (tid == 0 && sh_ok) {
         sh_ok = mbar_wait_bounded(&bar_mma[bp], php) ? 1 : 0;
         if (!sh_ok) atomicOr(status, ST_TIMEOUT);
@@ -328,25 +347,27 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
           issue_b(bp, Jbeg + p + 2);
         }
         if (sh_ok) {
-          sh_ok = mbar_wait_bounded(&bar_c[bp], php) ? 1 : 0;
+          sh_ok = mbar_wait_bounded(&bar_c[cp], phc) ? 1 : 0;
           if (!sh_ok) atomicOr(status, ST_TIMEOUT);
-          else nc_wait[bp]++;
+          else nc_wait[cp]++;
         }
       }
       __syncthreads();
       if (!sh_ok) { ok = false; break; }
       mbar_wait_bounded(&bar_mma[bp], php);
-      mbar_wait_bounded(&bar_c[bp], php);
+      mbar_wait_bounded(&bar_c[cp], phc);
       fence_after_sync();
-      // element (lr, 32 colh + q) of a tile sits at row_base + (q >> 3) * 256 + v[q & 7]
-      const int row_base = ((lr >> 5) * 8 + 4 * colh) * 256 + (lr & 3);
-      const float* cs = stage_c(bp) + (row < 64 ? 0 : TILE_ELEMS) + row_base;
+      // element (lr, TC_CW colg + q) of a tile sits at row_base + (q >> 3) * 256 + v[q & 7]
+      const int row_base = ((lr >> 5) * 8 + (TC_CW / 8) * colg) * 256 + (lr & 3);
+      const float* cs = stage_c(cp) + (row < 64 ? 0 : TILE_ELEMS) + row_base;
       float* ct = a + tile_base(m, row < 64 ? I0 : I1, Jbeg + p) + row_base;
-      float d[32];
-      tmem_ld32(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bp * TC_TMEM_COLS + 32 * colh), d);
+      float d[TC_CW];
+      const uint32_t tcol = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bp * TC_TMEM_COLS + TC_CW * colg);
+      if constexpr (TC_CW == 32) tmem_ld32(tcol, d);
+      else tmem_ld16(tcol, d);
       if (mine) {
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < TC_CW; ++q) {
           const int o = (q >> 3) * 256 + v_line[q & 7];
           ct[o] = cs[o] - d[q];
         }
@@ -354,7 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
       fence_before_sync();
       fence_proxy_async();
       __syncthreads();                          // accumulator buffer and C stage read
-      if (tid == 0 && p + 2 < nJ) issue_c(bp, Jbeg + p + 2);
+      if (tid == 0 && p + NC < nJ) issue_c(cp, Jbeg + p + NC);
     }
   }
   // after an abort: wait (bounded) for this CTA's own copies and tensor-core work still in
@@ -363,9 +384,10 @@ __global__ void __launch_bounds__(TC_THREADS) lu_update_tc_kernel(float* a, cons
     if (!a_done) mbar_wait_bounded(&bar_a, 0);
     for (int b = 0; b < 2; ++b) {
       for (; nb_wait[b] < nb_iss[b]; ++nb_wait[b]) mbar_wait_bounded(&bar_b[b], (uint32_t)nb_wait[b] & 1);
-      for (; nc_wait[b] < nc_iss[b]; ++nc_wait[b]) mbar_wait_bounded(&bar_c[b], (uint32_t)nc_wait[b] & 1);
       for (; nm_wait[b] < nm_iss[b]; ++nm_wait[b]) mbar_wait_bounded(&bar_mma[b], (uint32_t)nm_wait[b] & 1);
     }
+    for (int b = 0; b < NC; ++b)
+      for (; nc_wait[b] < nc_iss[b]; ++nc_wait[b]) mbar_wait_bounded(&bar_c[b], (uint32_t)nc_wait[b] & 1);
   }
   fence_before_sync();
   __syncthreads();
@@ -390,11 +412,11 @@ cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStre
   unsigned char* ub = (unsigned char*)f.ubuf;
   if (bf16) {
     lu_split_u_kernel<1><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub);
-    lu_update_tc_kernel<1><<<g, TC_THREADS, 1024 + TcSmem<1>::TOTAL, s>>>((float*)f.a, f.meta, ub, step, jchunk,
+    lu_update_tc_kernel<1><<<g, tc_threads<1>(), 1024 + TcSmem<1>::TOTAL, s>>>((float*)f.a, f.meta, ub, step, jchunk,
                                                                           f.status);
   } else {
     lu_split_u_kernel<2><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub);
-    lu_update_tc_kernel<2><<<g, TC_THREADS, 1024 + TcSmem<2>::TOTAL, s>>>((float*)f.a, f.meta, ub, step, jchunk,
+    lu_update_tc_kernel<2><<<g, tc_threads<2>(), 1024 + TcSmem<2>::TOTAL, s>>>((float*)f.a, f.meta, ub, step, jchunk,
                                                                           f.status);
   }
   return cudaGetLastError();
