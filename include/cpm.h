@@ -179,7 +179,7 @@ typedef struct {
   int transmission;
   int64_t max_n;              /* largest local size n_j */
   int64_t sum_n;              /* sum of n_j */
-  int64_t sum_n2;             /* sum of n_j^2 (algorithmic factor entries) */
+  int64_t sum_n2;             /* sum of n_j^2 (entries of the dense local matrices) */
   int64_t sum_sigma;          /* sum of |Sigma_j| (restrict reads) */
   int64_t factor_bytes;       /* device bytes of the resident factors */
   int64_t device_bytes;       /* all device bytes held by the handle */
@@ -192,6 +192,10 @@ typedef struct {
   int solve_prefetch;
   int solve_stagger;
   int64_t peak_device_bytes;  /* largest device_bytes reached so far (setup included) */
+  int64_t tile_rows;          /* 64-row tile rows over all subdomains (sum of T_j) */
+  int64_t solve_offdiag_tiles;/* off-diagonal 64 x 64 factor tiles one solve streams: the
+                                 tile envelope of L and U (local unknowns in reverse
+                                 Cuthill-McKee order); tiles outside it are exactly zero */
 } oras_info;
 cpm_status oras_info_get(const oras_precond* pc, oras_info* out);
 /* Device-memory plan of an oras_setup call, computed on the host without touching a GPU

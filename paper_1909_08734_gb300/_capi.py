@@ -51,7 +51,8 @@ class oras_info(C.Structure):
                 ("setup_ms_assemble", C.c_double), ("setup_ms_factor", C.c_double),
                 ("kernel_launches", C.c_int64), ("solve_ctas_per_sm", C.c_int),
                 ("solve_kseg", C.c_int), ("solve_prefetch", C.c_int), ("solve_stagger", C.c_int),
-                ("peak_device_bytes", C.c_int64)]
+                ("peak_device_bytes", C.c_int64), ("tile_rows", C.c_int64),
+                ("solve_offdiag_tiles", C.c_int64)]
 
 
 class oras_plan_info(C.Structure):

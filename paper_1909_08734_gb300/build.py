@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcpm_gb300.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-HOST_SRC = ["host/band.cpp", "host/partition.cpp", "host/local_coo.cpp", "capi_host.cpp"]
+HOST_SRC = ["host/band.cpp", "host/partition.cpp", "host/local_coo.cpp", "host/ordering.cpp", "capi_host.cpp"]
 CUDA_SRC = ["cuda/apply.cu", "cuda/factor.cu", "cuda/lu_tc.cu", "cuda/trsv.cu", "cuda/krylov.cu",
             "cuda/stationary.cu", "cuda/selftest.cu", "capi_device.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

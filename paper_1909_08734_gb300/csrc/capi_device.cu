@@ -64,6 +64,8 @@ struct oras_precond {
   std::vector<int64_t> n_local, n_sigma;
   std::vector<SubMeta> meta;
   int64_t sum_n = 0, sum_n2 = 0, sum_sigma = 0, rows_total = 0, tiles_total = 0;
+  std::vector<int32_t> tlo, thi;   // per tile row: nonzero L tiles [tlo, I), U tiles (I, thi]
+  int64_t solve_offdiag_tiles = 0;
   double ms_assemble = 0, ms_factor = 0;
   int64_t launches = 0;       // kernels launched after setup (graph nodes included)
   int solve_ctas = 0;         // current CTAs per SM of the batched solve
@@ -161,7 +163,8 @@ cpm_status set_schedule(oras_precond* pc, int ctas_per_sm, int kseg, int prefetc
     std::vector<int> Ts(pc->n_sub);
     for (int j = 0; j < pc->n_sub; ++j) Ts[j] = pc->meta[j].T;
     int maxseg = 1;
-    trsv_build_items(Ts.data(), pc->n_sub, kseg, stagger, items, &maxseg);
+    trsv_build_items(Ts.data(), pc->n_sub, kseg, stagger, items, &maxseg,
+                     pc->tlo.empty() ? nullptr : pc->tlo.data(), pc->thi.empty() ? nullptr : pc->thi.data());
     if (t.items) pc->release(const_cast<int2*>(t.items));
     if (t.ptag) pc->release(t.ptag);
     t.items = nullptr;
@@ -225,6 +228,18 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
       cpm::set_error(errs[j]);
       return sts[j];
     }
+  // ---- host: fill-reducing order of every local operator (reverse Cuthill-McKee) ----
+  std::vector<std::vector<int32_t>> inv_order(ns);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < ns; ++j) {
+    std::vector<int32_t> perm;
+    cpm::rcm_order(coo[j], perm);
+    std::vector<int32_t>& inv = inv_order[j];
+    inv.resize(coo[j].n);
+    for (int64_t k = 0; k < coo[j].n; ++k) inv[perm[k]] = (int32_t)k;
+    for (auto& r : coo[j].row) r = inv[r];
+    for (auto& cc : coo[j].col) cc = inv[cc];
+  }
   pc->meta.resize(ns);
   pc->n_local.resize(ns);
   pc->n_sigma.resize(ns);
@@ -253,6 +268,21 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   pc->t_max = t_max;
   pc->rows_total = row_off;
   pc->tiles_total = tile_off / TILE_ELEMS;
+  // tile envelope of the factors: per row first / last tile column, per step the panel's rows
+  std::vector<int32_t> h_first(row_off), h_last(row_off), h_pend((size_t)ns * t_max, 0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < ns; ++j) {
+    const SubMeta& m = pc->meta[j];
+    std::vector<int32_t> f, l, pe;
+    cpm::envelope(coo[j], m.T, f, l, pe);
+    std::copy(f.begin(), f.end(), h_first.begin() + m.row_off);
+    std::copy(l.begin(), l.end(), h_last.begin() + m.row_off);
+    std::copy(pe.begin(), pe.end(), h_pend.begin() + (size_t)j * t_max);
+  }
+  std::vector<int32_t> step_rows(t_max, 64);
+  for (int j = 0; j < ns; ++j)
+    for (int st2 = 0; st2 < pc->meta[j].T; ++st2)
+      step_rows[st2] = std::max(step_rows[st2], h_pend[(size_t)j * t_max + st2] - 64 * st2);
   const bool fp64 = precision == CPM_FP64;
   const size_t wbytes = fp64 ? 8 : 4;
 
@@ -284,10 +314,13 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
       const cpm::SubSets& S = P.subs[j];
       unk_off[j] = o;
       for (int32_t g : S.own) mine[g] = 1;
+      // local unknown t (Sigma_j, then Sigma_j^{BC,A}) sits at position inv[t] of the order;
+      // flags: 1 = in the disjoint set (prolonged), 2 = in Sigma_j (carries the residual)
+      const std::vector<int32_t>& inv = inv_order[j];
       int64_t t = 0;
-      for (int32_t g : S.sigma) { unknowns[o + t] = g; own[o + t] = mine[g]; ++t; }
+      for (int32_t g : S.sigma) { unknowns[o + inv[t]] = g; own[o + inv[t]] = mine[g] | 2; ++t; }
       if (transmission != CPM_RAS)
-        for (int32_t g : S.bc_a) { unknowns[o + t] = g; own[o + t] = 0; ++t; }
+        for (int32_t g : S.bc_a) { unknowns[o + inv[t]] = g; own[o + inv[t]] = 0; ++t; }
       for (int32_t g : S.own) mine[g] = 0;
       o += pc->n_local[j];
     }
@@ -341,6 +374,19 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   CK(launch_scatter(work, fp64, d_off, d_val, nnz, s));
   CK(cudaEventRecord(e1, s));
   FactorDev f{work, pc->d_meta, ipiv, pc->status, ns, t_max, fp64 ? 1 : 0};
+  int32_t *d_first, *d_last, *d_pend, *d_hiu;
+  ALLOC(d_first, int32_t, row_off);
+  ALLOC(d_last, int32_t, row_off);
+  ALLOC(d_pend, int32_t, (int64_t)ns * t_max);
+  ALLOC(d_hiu, int32_t, ns);
+  CK(cudaMemcpyAsync(d_first, h_first.data(), 4 * (size_t)row_off, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_last, h_last.data(), 4 * (size_t)row_off, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_pend, h_pend.data(), 4 * h_pend.size(), cudaMemcpyHostToDevice, s));
+  f.first = d_first;
+  f.last = d_last;
+  f.pend = d_pend;
+  f.hiu = d_hiu;
+  f.step_rows = step_rows.data();
   // FP32: split-tf32 tensor-core update (FP32 accuracy); BF16: bf16 inputs, FP32 accumulate
   const int use_tc = (precision == CPM_FP64 || simt_lu) ? 0 : (precision == CPM_BF16 ? 2 : 1);
   void* ubuf = nullptr;
@@ -378,6 +424,31 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   pc->release(d_unk_off);
   pc->release(ipiv);
   if (ubuf) pc->release(ubuf);
+  // final envelope: per tile row the first nonzero L tile and the last nonzero U tile
+  CK(cudaMemcpy(h_first.data(), d_first, 4 * (size_t)row_off, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(h_last.data(), d_last, 4 * (size_t)row_off, cudaMemcpyDeviceToHost));
+  pc->release(d_first);
+  pc->release(d_last);
+  pc->release(d_pend);
+  pc->release(d_hiu);
+  const int64_t n_trow = row_off / TILE;
+  pc->tlo.assign(n_trow, 0);
+  pc->thi.assign(n_trow, 0);
+  pc->solve_offdiag_tiles = 0;
+  for (int j = 0; j < ns; ++j) {
+    const SubMeta& m = pc->meta[j];
+    for (int I = 0; I < m.T; ++I) {
+      const int64_t tr = (m.row_off >> 6) + I;
+      int32_t lo = I, hi = I;
+      for (int r = 0; r < TILE; ++r) {
+        lo = std::min(lo, h_first[m.row_off + 64 * I + r]);
+        hi = std::max(hi, h_last[m.row_off + 64 * I + r]);
+      }
+      pc->tlo[tr] = lo;
+      pc->thi[tr] = std::min(hi, m.T - 1);
+      pc->solve_offdiag_tiles += (I - lo) + (pc->thi[tr] - I);
+    }
+  }
   int hst = 0;
   CK(cudaMemcpy(&hst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (hst & ST_SINGULAR) {
@@ -419,6 +490,15 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   t.status = pc->status;
   t.precision = precision;
   t.nr_cap = 1;
+  {
+    int32_t *d_tlo, *d_thi;
+    ALLOC(d_tlo, int32_t, n_trow);
+    ALLOC(d_thi, int32_t, n_trow);
+    CK(cudaMemcpy(d_tlo, pc->tlo.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(d_thi, pc->thi.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
+    t.tlo = d_tlo;
+    t.thi = d_thi;
+  }
   CK(trsv_prepare(precision));
   st = set_schedule(pc, trsv_ctas_per_sm(precision), 1023, 0, 0);
   if (st != CPM_OK) return st;
@@ -717,6 +797,8 @@ cpm_status oras_info_get(const oras_precond* pc, oras_info* o) {
   o->solve_prefetch = pc->trsv.prefetch;
   o->solve_stagger = pc->trsv.stagger;
   o->peak_device_bytes = (int64_t)pc->peak_bytes;
+  o->tile_rows = pc->rows_total / TILE;
+  o->solve_offdiag_tiles = pc->solve_offdiag_tiles;
   return CPM_OK;
 }
 
@@ -776,9 +858,10 @@ cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmissio
                         rnd(8 * nblk * (restart + 2)) + rnd(8 * (int64_t)(restart + 2) * (restart + 8) + 4096) +
                         rnd(64) + rnd(8 * NN) /* extension values */ + rnd(8 * nrhs * NN) /* apply scratch */;
   const int64_t ubuf = precision == CPM_FP64 ? 0 : rnd((int64_t)lu_tc_ubuf_bytes(rows / TILE, precision == CPM_BF16));
-  const int64_t setup_peak = band_dev + work + inv + small + assembly + ubuf +
+  const int64_t envelope = 2 * rnd(4 * rows) + rnd(4 * (int64_t)ns * t_max) + rnd(4 * ns);
+  const int64_t setup_peak = band_dev + work + inv + small + assembly + ubuf + envelope +
                              (precision == CPM_BF16 ? rnd(2 * tile_elems) : 0);
-  const int64_t resident = band_dev + rnd(factor) + inv + small + sched + gmres;
+  const int64_t resident = band_dev + rnd(factor) + inv + small + sched + gmres + 2 * rnd(4 * (rows / TILE));
   out->setup_peak_bytes = setup_peak + (setup_peak >> 6);
   out->resident_bytes = resident + (resident >> 6);
   out->factor_bytes = factor;

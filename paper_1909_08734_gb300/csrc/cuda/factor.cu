@@ -9,6 +9,7 @@
 //            tensor-core version lives in lu_tc.cu)
 // FP64 mode keeps double tiles; FP32 and BF16 modes keep float tiles in the swizzled
 // layout of common.cuh.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -67,10 +68,13 @@ constexpr int PANEL_THREADS = 512;
 
 template <typename T>
 __global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(T* a, const SubMeta* __restrict__ meta,
-                                                                 int32_t* ipiv, int* status, int s) {
+                                                                 int32_t* ipiv, int* status, int s,
+                                                                 const int32_t* __restrict__ pend, int t_max) {
   const SubMeta m = meta[blockIdx.x];
   if (s >= m.T) return;
-  const int np = 64 * m.T, k0 = 64 * s, tid = threadIdx.x;
+  const int k0 = 64 * s, tid = threadIdx.x;
+  // rows at or beyond np are zero in the panel's columns (tile envelope) and stay untouched
+  const int np = pend ? pend[blockIdx.x * t_max + s] : 64 * m.T;
   const int lane = tid & 31, warp = tid >> 5;
   __shared__ T prow[64];
   __shared__ double wv[PANEL_THREADS / 32];
@@ -173,7 +177,9 @@ __device__ __forceinline__ void block_argmax(double best, int bi, double* wv, in
 template <typename T>
 __global__ void __launch_bounds__(PC_THREADS) lu_panel_cluster_kernel(T* a, const SubMeta* __restrict__ meta,
                                                                       int32_t* ipiv, int* status, int s,
-                                                                      int rows_per_cta) {
+                                                                      int rows_per_cta,
+                                                                      const int32_t* __restrict__ pend,
+                                                                      int t_max) {
   constexpr int PC_STRIDE = PanelVec<T>::STRIDE;
   constexpr int VN = PanelVec<T>::N;
   using VT = typename PanelVec<T>::V;
@@ -192,7 +198,9 @@ __global__ void __launch_bounds__(PC_THREADS) lu_panel_cluster_kernel(T* a, cons
   __shared__ __align__(16) T prow[64];
   __shared__ int piv_sh, piv_rank, piv_slot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int k0 = 64 * s, np = 64 * m.T;
+  const int k0 = 64 * s;
+  // rows at or beyond np are zero in the panel's columns (tile envelope) and stay untouched
+  const int np = pend ? pend[(blockIdx.x / cs) * t_max + s] : 64 * m.T;
   const int r0 = k0 + rank * rows_per_cta;
   const int nr = max(0, min(np, r0 + rows_per_cta) - r0);
   for (int e = tid; e < nr * 64; e += PC_THREADS) {
@@ -335,7 +343,69 @@ static cudaError_t launch_panel_cluster(const FactorDev& f, int step, int cs, in
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T>, (T*)f.a, f.meta, f.ipiv, f.status, step, rpc);
+  return cudaLaunchKernelEx(&cfg, lu_panel_cluster_kernel<T>, (T*)f.a, f.meta, f.ipiv, f.status, step, rpc,
+                            f.pend, f.t_max);
+}
+
+// ---------------------------------------------------------------- tile envelope, step s
+// After the panel of step s: apply its 64 row interchanges to the rows' first / last tile
+// columns, take the U row's extent hiu = max last over the pivot block, and extend last to
+// hiu for every row below the block that the step updates (first <= s).  Rows [k0, pend)
+// are staged in shared memory (ENV_SMEM_ROWS at most; beyond that the kernel works in
+// global memory).
+constexpr int ENV_THREADS = 256;
+constexpr int ENV_SMEM_ROWS = 16384;
+__global__ void __launch_bounds__(ENV_THREADS) lu_envelope_kernel(int32_t* first, int32_t* last,
+                                                                 const SubMeta* __restrict__ meta,
+                                                                 const int32_t* __restrict__ ipiv,
+                                                                 const int32_t* __restrict__ pend, int t_max,
+                                                                 int s, int32_t* hiu, int* status) {
+  const SubMeta m = meta[blockIdx.x];
+  if (s >= m.T) return;
+  const int k0 = 64 * s, tid = threadIdx.x;
+  const int nrow = pend[blockIdx.x * t_max + s] - k0;
+  extern __shared__ int32_t env_smem[];
+  const bool staged = nrow <= ENV_SMEM_ROWS;
+  int32_t* F = staged ? env_smem : first + m.row_off + k0;
+  int32_t* Lr = staged ? env_smem + nrow : last + m.row_off + k0;
+  if (staged) {
+    for (int i = tid; i < nrow; i += ENV_THREADS) {
+      F[i] = first[m.row_off + k0 + i];
+      Lr[i] = last[m.row_off + k0 + i];
+    }
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int c = 0; c < 64; ++c) {
+      const int p = ipiv[m.row_off + k0 + c] - k0;
+      if (p < c || p >= nrow) {                // outside the panel's rows: cannot happen
+        atomicOr(status, ST_SINGULAR);
+        continue;
+      }
+      const int32_t tf = F[c], tl = Lr[c];
+      F[c] = F[p];
+      Lr[c] = Lr[p];
+      F[p] = tf;
+      Lr[p] = tl;
+    }
+  __syncthreads();
+  __shared__ int32_t hmax[ENV_THREADS / 32];
+  int32_t h = tid < 64 ? Lr[tid] : s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
+  if ((tid & 31) == 0) hmax[tid >> 5] = h;
+  __syncthreads();
+  int32_t hu = s;
+  for (int w = 0; w < ENV_THREADS / 32; ++w) hu = max(hu, hmax[w]);
+  if (tid == 0) hiu[blockIdx.x] = hu;
+  for (int i = 64 + tid; i < nrow; i += ENV_THREADS)
+    if (F[i] <= s && Lr[i] < hu) Lr[i] = hu;
+  __syncthreads();
+  if (staged)
+    for (int i = tid; i < nrow; i += ENV_THREADS) {
+      first[m.row_off + k0 + i] = F[i];
+      last[m.row_off + k0 + i] = Lr[i];
+    }
 }
 
 // Largest cluster size the device can co-schedule with the panel kernel's shared memory.
@@ -343,6 +413,9 @@ static int g_panel_max_cs[2] = {0, 0};
 
 cudaError_t lu_panel_prepare() {
   cudaError_t e;
+  e = cudaFuncSetAttribute(lu_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(ENV_SMEM_ROWS * 2 * sizeof(int32_t)));
+  if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_panel_cluster_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, PC_SMEM);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(lu_panel_cluster_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, PC_SMEM);
@@ -398,10 +471,11 @@ __global__ void lu_swap_kernel(T* a, const SubMeta* __restrict__ meta, const int
 
 // ---------------------------------------------------------------- U_sJ = L_ss^{-1} A_sJ
 template <typename T>
-__global__ void __launch_bounds__(64) lu_trsm_kernel(T* a, const SubMeta* __restrict__ meta, int s) {
+__global__ void __launch_bounds__(64) lu_trsm_kernel(T* a, const SubMeta* __restrict__ meta, int s,
+                                                     const int32_t* __restrict__ hiu) {
   const SubMeta m = meta[blockIdx.y];
   const int J = s + 1 + blockIdx.x;
-  if (J >= m.T) return;
+  if (J >= m.T || (hiu && J > hiu[blockIdx.y])) return;   // zero tiles of the U row stay zero
   __shared__ T L[64][65];
   const T* ts = a + tile_base(m, s, s);
   for (int e = threadIdx.x; e < 4096; e += 64) {
@@ -428,11 +502,14 @@ __global__ void __launch_bounds__(64) lu_trsm_kernel(T* a, const SubMeta* __rest
 // ---------------------------------------------------------------- A_IJ -= L_Is U_sJ (SIMT)
 template <typename T>
 __global__ void __launch_bounds__(256) lu_update_simt_kernel(T* a, const SubMeta* __restrict__ meta,
-                                                             int s, int t_max) {
+                                                             int s, int t_max, const int32_t* __restrict__ pend,
+                                                             const int32_t* __restrict__ hiu) {
   const SubMeta m = meta[blockIdx.y];
   const int W = t_max - 1 - s;
   const int I = s + 1 + blockIdx.x / W, J = s + 1 + blockIdx.x % W;
   if (I >= m.T || J >= m.T) return;
+  // outside the envelope L_Is or U_sJ is zero: the tile does not change
+  if (pend && (64 * I >= pend[blockIdx.y * t_max + s] || J > hiu[blockIdx.y])) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* As = (T*)smem_raw;              // As[i*65 + k]
   T* Bs = As + 64 * 65;              // Bs[k*65 + j]
@@ -473,23 +550,35 @@ __global__ void __launch_bounds__(256) lu_update_simt_kernel(T* a, const SubMeta
 
 cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_t s) {
   const int W = f.t_max - 1 - step;
+  const bool env = f.pend != nullptr;
+  // panel rows of this step: the largest envelope range over the subdomains
+  const int max_rows = env ? f.step_rows[step] : 64 * (f.t_max - step);
   int rpc = 0;
-  const int cs = panel_cluster_size(64 * (f.t_max - step), f.fp64 ? 8 : 4, &rpc);
+  const int cs = panel_cluster_size(max_rows, f.fp64 ? 8 : 4, &rpc);
   const bool cluster = cs > 0 && cs <= g_panel_max_cs[f.fp64 ? 1 : 0];
+  const size_t sm = 2 * 64 * 65 * (f.fp64 ? sizeof(double) : sizeof(float));
+  const size_t env_smem = (size_t)std::min(max_rows, ENV_SMEM_ROWS) * 2 * sizeof(int32_t);
+  auto envelope = [&]() {
+    if (env)
+      lu_envelope_kernel<<<f.n_sub, ENV_THREADS, env_smem, s>>>(f.first, f.last, f.meta, f.ipiv, f.pend,
+                                                                f.t_max, step, f.hiu, f.status);
+  };
   if (f.fp64) {
     double* a = (double*)f.a;
     if (cluster) {
       cudaError_t e = launch_panel_cluster<double>(f, step, cs, rpc, s);
       if (e != cudaSuccess) return e;
     } else {
-      lu_panel_kernel<double><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+      lu_panel_kernel<double><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step, f.pend,
+                                                                f.t_max);
     }
+    envelope();
     lu_swap_kernel<double><<<dim3(f.t_max, f.n_sub), 64, 0, s>>>(a, f.meta, f.ipiv, step);
     if (W > 0) {
-      lu_trsm_kernel<double><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step);
-      size_t sm = 2 * 64 * 65 * sizeof(double);
+      lu_trsm_kernel<double><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step, f.hiu);
       cudaFuncSetAttribute(lu_update_simt_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      lu_update_simt_kernel<double><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max);
+      lu_update_simt_kernel<double><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max, f.pend,
+                                                                          f.hiu);
     }
   } else {
     float* a = (float*)f.a;
@@ -497,17 +586,19 @@ cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_
       cudaError_t e = launch_panel_cluster<float>(f, step, cs, rpc, s);
       if (e != cudaSuccess) return e;
     } else {
-      lu_panel_kernel<float><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step);
+      lu_panel_kernel<float><<<f.n_sub, PANEL_THREADS, 0, s>>>(a, f.meta, f.ipiv, f.status, step, f.pend,
+                                                               f.t_max);
     }
+    envelope();
     lu_swap_kernel<float><<<dim3(f.t_max, f.n_sub), 64, 0, s>>>(a, f.meta, f.ipiv, step);
     if (W > 0) {
-      lu_trsm_kernel<float><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step);
+      lu_trsm_kernel<float><<<dim3(W, f.n_sub), 64, 0, s>>>(a, f.meta, step, f.hiu);
       if (use_tc) {
         cudaError_t e = launch_lu_update_tc(f, step, use_tc == 2, s);
         if (e != cudaSuccess) return e;
       } else {
-        size_t sm = 2 * 64 * 65 * sizeof(float);
-        lu_update_simt_kernel<float><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max);
+        lu_update_simt_kernel<float><<<dim3(W * W, f.n_sub), 256, sm, s>>>(a, f.meta, step, f.t_max, f.pend,
+                                                                           f.hiu);
       }
     }
   }
@@ -516,8 +607,9 @@ cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_
 
 // ---------------------------------------------------------------- after the factorisation
 // perm: the row interchanges applied in order to the identity; gather[r] = global index of
-// local unknown perm[r] when it carries residual (first n_sigma unknowns), else -1;
-// scatter[r] = global index of local unknown r if r is in the disjoint set, else -1;
+// local unknown perm[r] when it carries residual (own_flag bit 2: in Sigma_j), else -1;
+// scatter[r] = global index of local unknown r if r is in the disjoint set (own_flag bit 1),
+// else -1;
 // dinv[r] = 1 / U_rr.
 template <typename T>
 __global__ void lu_finish_kernel(const T* a, const SubMeta* __restrict__ meta, const int32_t* ipiv,
@@ -538,8 +630,8 @@ __global__ void lu_finish_kernel(const T* a, const SubMeta* __restrict__ meta, c
   const int64_t uo = unk_off[blockIdx.x];
   for (int r = threadIdx.x; r < np; r += blockDim.x) {
     int pr = perm[r];
-    perm[r] = pr < m.n_sigma ? unknowns[uo + pr] : -1;
-    scatter[m.row_off + r] = (r < m.n && own_flag[uo + r]) ? unknowns[uo + r] : -1;
+    perm[r] = (pr < m.n && (own_flag[uo + pr] & 2)) ? unknowns[uo + pr] : -1;
+    scatter[m.row_off + r] = (r < m.n && (own_flag[uo + r] & 1)) ? unknowns[uo + r] : -1;
     T d = at(a, m, r, r);
     dinv[m.row_off + r] = d != (T)0 ? (T)1 / d : (T)0;
   }

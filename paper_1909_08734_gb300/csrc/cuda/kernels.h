@@ -72,6 +72,12 @@ struct FactorDev {
   int fp64;                // 1: double tiles, 0: float (swizzled) tiles
   void* ubuf = nullptr;    // tensor-core update: the step's U row split into MMA operands
                            // (lu_tc_ubuf_bytes(rows_total / 64, bf16) bytes)
+  // tile envelope of the factors (rows in the order the factorisation leaves them):
+  int32_t* first = nullptr;        // per padded row: first nonzero tile column (moves with the row)
+  int32_t* last = nullptr;         // per padded row: last tile column that can be nonzero
+  const int32_t* pend = nullptr;   // [subdomain * t_max + s]: rows with first <= s lie below this
+  int32_t* hiu = nullptr;          // per subdomain: last nonzero tile column of the step's U row
+  const int32_t* step_rows = nullptr;   // host, per step: max over subdomains of pend - 64 s
 };
 cudaError_t launch_scatter(void* a, int fp64, const int64_t* off, const double* val, int64_t nnz,
                            cudaStream_t s);
@@ -114,6 +120,8 @@ struct TrsvDev {
   int precision;           // 0 fp64, 1 fp32, 2 bf16
   int grid;
   int nr_cap;              // right-hand sides the tagged-word buffers hold per row
+  const int32_t* tlo;      // per tile row (row_off / 64 + I): first nonzero L tile column (or null: 0)
+  const int32_t* thi;      // per tile row: last nonzero U tile column (or null: T - 1)
 };
 constexpr int TRSV_MAX_NR = 8;
 // nr in {1, 2, 4, 8} right-hand sides (r_in / z_out columns) per launch, nr <= t.nr_cap
@@ -123,9 +131,10 @@ int trsv_ctas_per_sm(int precision);
 cudaError_t trsv_prepare(int precision);
 // Queue of work items for the batched solve: forward items, then backward items, each
 // sorted by the chain position they wait for (partial segments of a row before its
-// diagonal item).  T[j] = tiles per dimension of subdomain j.
+// diagonal item).  T[j] = tiles per dimension of subdomain j; tlo / thi (per tile row, in
+// subdomain order) bound each row's nonzero L and U tiles (null: the dense triangle).
 void trsv_build_items(const int* T, int n_sub, int kseg, int stagger, std::vector<int2>& items,
-                      int* maxseg);
+                      int* maxseg, const int32_t* tlo = nullptr, const int32_t* thi = nullptr);
 
 // ---- Krylov kernels ----
 struct GmresDev {

@@ -18,6 +18,8 @@
 //              lock step per column, two CTAs per SM, results leave by bulk copies.
 // Every wait is bounded; on expiry the CTA reports CPM_ERR_TIMEOUT, waits (bounded) for its
 // own copies and MMAs in flight, frees its tensor memory, and returns.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -176,10 +178,11 @@ template <> struct TcSmem<1> {    // A bf16 16 KB, B stages NB x bf16 8 KB, C st
 // row_off/64 + J of the buffer holds tile (s, J) of that subdomain.
 template <int KIND>
 __global__ void __launch_bounds__(256) lu_split_u_kernel(const float* __restrict__ a, const SubMeta* __restrict__ meta,
-                                                         int s, unsigned char* __restrict__ ubuf) {
+                                                         int s, unsigned char* __restrict__ ubuf,
+                                                         const int32_t* __restrict__ hiu) {
   const SubMeta m = meta[blockIdx.y];
   const int J = s + 1 + blockIdx.x;
-  if (J >= m.T) return;
+  if (J >= m.T || (hiu && J > hiu[blockIdx.y])) return;
   const float* t = a + tile_base(m, s, J);
   unsigned char* dst = ubuf + (size_t)((m.row_off >> 6) + J) * TcSmem<KIND>::BBYTES;
   if (KIND == 2) {
@@ -207,7 +210,9 @@ __global__ void __launch_bounds__(256) lu_split_u_kernel(const float* __restrict
 template <int KIND>
 __global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float* a, const SubMeta* __restrict__ meta,
                                                                    const unsigned char* __restrict__ ubuf, int s,
-                                                                   int jchunk, int* status) {
+                                                                   int jchunk, int* status,
+                                                                   const int32_t* __restrict__ pend,
+                                                                   const int32_t* __restrict__ hiu, int t_max) {
   using L = TcSmem<KIND>;
   constexpr int TC_THREADS = tc_threads<KIND>();
   constexpr int TC_CG = TC_THREADS / 128;      // epilogue column groups (warps per lane quarter)
@@ -215,8 +220,14 @@ __global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float*
   const SubMeta m = meta[blockIdx.z];
   const int I0 = s + 1 + 2 * blockIdx.x, I1 = I0 + 1;
   const int Jbeg = s + 1 + blockIdx.y * jchunk;
-  if (I0 >= m.T || Jbeg >= m.T) return;        // before any tensor-memory allocation
-  const int nJ = min(m.T, Jbeg + jchunk) - Jbeg;
+  // tile envelope: L_Is is zero for tile rows past pend, U_sJ for columns past hiu
+  int Tend = m.T;
+  if (pend) {
+    if (64 * I0 >= pend[blockIdx.z * t_max + s]) return;
+    Tend = min(Tend, hiu[blockIdx.z] + 1);
+  }
+  if (I0 >= m.T || Jbeg >= Tend) return;       // before any tensor-memory allocation
+  const int nJ = min(Tend, Jbeg + jchunk) - Jbeg;
   const bool two = I1 < m.T;
   const uint32_t pair_bytes = two ? 32768u : 16384u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -445,7 +456,8 @@ __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile
 template <int EPI>
 __global__ void __launch_bounds__(128 + 32 * EPI, 1)
     lu_update_ws_kernel(float* a, const SubMeta* __restrict__ meta, const unsigned char* __restrict__ ubuf, int s,
-                        int jchunk, int* status) {
+                        int jchunk, int* status, const int32_t* __restrict__ pend, const int32_t* __restrict__ hiu,
+                        int t_max) {
   using L = TcSmem<2>;
   constexpr int NT = 128 + 32 * EPI, NB = (int)L::NB, NC = (int)L::NC;
   constexpr int CW = 64 / (EPI / 4);            // accumulator columns per epilogue warp
@@ -453,8 +465,14 @@ __global__ void __launch_bounds__(128 + 32 * EPI, 1)
   const SubMeta m = meta[blockIdx.z];
   const int I0 = s + 1 + 2 * blockIdx.x, I1 = I0 + 1;
   const int Jbeg = s + 1 + blockIdx.y * jchunk;
-  if (I0 >= m.T || Jbeg >= m.T) return;        // before any tensor-memory allocation
-  const int nJ = min(m.T, Jbeg + jchunk) - Jbeg;
+  // tile envelope: L_Is is zero for tile rows past pend, U_sJ for columns past hiu
+  int Tend = m.T;
+  if (pend) {
+    if (64 * I0 >= pend[blockIdx.z * t_max + s]) return;
+    Tend = min(Tend, hiu[blockIdx.z] + 1);
+  }
+  if (I0 >= m.T || Jbeg >= Tend) return;       // before any tensor-memory allocation
+  const int nJ = min(Tend, Jbeg + jchunk) - Jbeg;
   const bool two = I1 < m.T;
   const uint32_t pair_bytes = two ? 32768u : 16384u;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -661,17 +679,20 @@ cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStre
   if (W <= 0) return cudaSuccess;
   if (!f.ubuf) return cudaErrorInvalidValue;
   if (jchunk < 1) jchunk = TC_JCHUNK;
+  // tile rows below the pivot block that the step can update (tile envelope)
+  const int WR = f.pend ? std::min(W, (f.step_rows[step] + 63) / 64 - 1) : W;
+  if (WR <= 0) return cudaSuccess;
   dim3 gs(W, f.n_sub);
-  dim3 g((W + 1) / 2, (W + jchunk - 1) / jchunk, f.n_sub);
+  dim3 g((WR + 1) / 2, (W + jchunk - 1) / jchunk, f.n_sub);
   unsigned char* ub = (unsigned char*)f.ubuf;
   if (bf16) {
-    lu_split_u_kernel<1><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub);
-    lu_update_tc_kernel<1><<<g, tc_threads<1>(), 1024 + TcSmem<1>::TOTAL, s>>>((float*)f.a, f.meta, ub, step, jchunk,
-                                                                          f.status);
+    lu_split_u_kernel<1><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub, f.hiu);
+    lu_update_tc_kernel<1><<<g, tc_threads<1>(), 1024 + TcSmem<1>::TOTAL, s>>>(
+        (float*)f.a, f.meta, ub, step, jchunk, f.status, f.pend, f.hiu, f.t_max);
   } else {
-    lu_split_u_kernel<2><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub);
+    lu_split_u_kernel<2><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub, f.hiu);
     lu_update_ws_kernel<TC_WS_EPI><<<g, 128 + 32 * TC_WS_EPI, 1024 + TcSmem<2>::TOTAL, s>>>(
-        (float*)f.a, f.meta, ub, step, jchunk, f.status);
+        (float*)f.a, f.meta, ub, step, jchunk, f.status, f.pend, f.hiu, f.t_max);
   }
   return cudaGetLastError();
 }

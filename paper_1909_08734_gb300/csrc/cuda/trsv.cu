@@ -106,8 +106,8 @@ __device__ __forceinline__ bool poll_value(const uint64_t* p, uint32_t tag, C* v
 // Decoded work item.
 struct Item {
   int j, I, seg, bwd;
-  int T, p, nseg, q0, nq, nload;
-  bool diag;
+  int T, p, jb, nseg, q0, nq, nload;   // off-diagonal tile q sits in column jb + q (forward)
+  bool diag;                           // or jb - q (backward)
 };
 
 template <int PIECES>
@@ -120,7 +120,15 @@ __device__ __forceinline__ Item decode(const TrsvDev& t, int idx) {
   e.bwd = (it.y >> 30) & 1;
   e.diag = e.seg == SEG_DIAG;
   e.T = t.meta[e.j].T;
-  e.p = e.bwd ? e.T - 1 - e.I : e.I;
+  // tile envelope of the row: L tiles [tlo, I), U tiles (I, thi]; tiles outside are zero
+  const int64_t trow = (t.meta[e.j].row_off >> 6) + e.I;
+  if (e.bwd) {
+    e.jb = t.thi ? t.thi[trow] : e.T - 1;
+    e.p = e.jb - e.I;
+  } else {
+    e.jb = t.tlo ? t.tlo[trow] : 0;
+    e.p = e.I - e.jb;
+  }
   const int K = t.kseg;
   e.nseg = e.p > 0 ? (e.p + K - 1) / K : 1;
   e.q0 = e.diag ? (e.nseg - 1) * K : e.seg * K;
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
     const SubMeta m = t.meta[e.j];
     if (l < e.nq) {
       const int q = e.q0 + l;
-      const int J = e.bwd ? e.T - 1 - q : q;
+      const int J = e.bwd ? e.jb - q : e.jb + q;
       bulk_g2s(dst, tiles + tile_base(m, e.I, J), STAGE, &bar[st]);
     } else {
       const int64_t trow = (m.row_off >> 6) + e.I;
@@ -242,7 +250,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
     // tagged words of the solved piece multiplying off-diagonal tile l of this item
     auto ywords = [&](int l, int q) {
       const int qq = e.q0 + l;
-      const int J = e.bwd ? e.T - 1 - qq : qq;
+      const int J = e.bwd ? e.jb - qq : e.jb + qq;
       return t.ytag + ((m.row_off + 64 * J + tid) * NR + q) * W;
     };
     auto pwords = [&](int seg, int q) { return t.ptag + (((trow * t.maxseg + seg) * 64 + tid) * NR + q) * W; };
@@ -417,22 +425,29 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
 // sweep overlap with bulk work of others.  Either way every dependency of an item sorts
 // before it.
 void trsv_build_items(const int* T, int n_sub, int kseg, int stagger, std::vector<int2>& items,
-                      int* maxseg) {
+                      int* maxseg, const int32_t* tlo, const int32_t* thi) {
   items.clear();
   int ms = 1;
   std::vector<std::tuple<int, int, int, int, int, int>> q;   // key, kind, j, I, seg, bwd
-  for (int bwd = 0; bwd < 2; ++bwd)
+  // key = the position in the sweep (forward: tile row, backward: T-1 - tile row) of the last
+  // solved piece the item waits for
+  for (int bwd = 0; bwd < 2; ++bwd) {
+    int64_t trow0 = 0;
     for (int j = 0; j < n_sub; ++j) {
       const int off = stagger ? ((j & 1) ? T[j] / 2 : 0) + (bwd ? T[j] : 0)
                               : (bwd ? 1 << 24 : 0);
       for (int I = 0; I < T[j]; ++I) {
-        const int p = bwd ? T[j] - 1 - I : I;
+        const int lo = tlo ? tlo[trow0 + I] : 0, hi = thi ? thi[trow0 + I] : T[j] - 1;
+        const int p = bwd ? hi - I : I - lo;
+        const int base = bwd ? T[j] - 1 - hi : lo;
         const int nseg = p > 0 ? (p + kseg - 1) / kseg : 1;
         ms = std::max(ms, nseg);
-        for (int s = 0; s < nseg - 1; ++s) q.emplace_back(off + s * kseg + kseg - 1, 0, j, I, s, bwd);
-        q.emplace_back(off + p - 1, 1, j, I, SEG_DIAG, bwd);
+        for (int s = 0; s < nseg - 1; ++s) q.emplace_back(off + base + s * kseg + kseg - 1, 0, j, I, s, bwd);
+        q.emplace_back(off + base + p - 1, 1, j, I, SEG_DIAG, bwd);
       }
+      trow0 += T[j];
     }
+  }
   std::sort(q.begin(), q.end());
   for (auto& e : q)
     items.push_back(make_int2(std::get<2>(e), std::get<3>(e) | (std::get<4>(e) << 20) | (std::get<5>(e) << 30)));

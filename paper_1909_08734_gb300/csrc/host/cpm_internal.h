@@ -102,6 +102,14 @@ struct LocalCOO {
   std::vector<double> val;
 };
 
+// Reverse Cuthill-McKee order of the pattern of A_j + A_j^T: perm[new] = old (deterministic).
+void rcm_order(const LocalCOO& L, std::vector<int32_t>& perm);
+// Tile envelope of the LU factors of a local operator with T tiles per dimension: per padded
+// row its first and last nonzero tile columns, and per step s one past the last position a
+// row with first <= s can take (the panel's row range).
+void envelope(const LocalCOO& L, int T, std::vector<int32_t>& first, std::vector<int32_t>& last,
+              std::vector<int32_t>& pend);
+
 cpm_status build_band(const Surface& s, double h, int p, double lam_over_h, Band& out);
 // Algorithmic band: the smallest node set containing the grid nodes within h of the surface
 // and the interpolation stencils of CP(x) for its nodes and their 6-neighbours.
