@@ -449,6 +449,14 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
       pc->solve_offdiag_tiles += (I - lo) + (pc->thi[tr] - I);
     }
   }
+  int32_t *d_tlo, *d_thi;
+  ALLOC(d_tlo, int32_t, n_trow);
+  ALLOC(d_thi, int32_t, n_trow);
+  CK(cudaMemcpy(d_tlo, pc->tlo.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_thi, pc->thi.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
+  // chain tiles of the solves: L_{I,I-1} and U_{I,I+1} premultiplied by the diagonal inverses
+  CK(launch_chain_tiles(work, fp64, pc->d_meta, ns, t_max, inv, d_tlo, d_thi, s));
+  CK(cudaStreamSynchronize(s));
   int hst = 0;
   CK(cudaMemcpy(&hst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (hst & ST_SINGULAR) {
@@ -490,15 +498,8 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   t.status = pc->status;
   t.precision = precision;
   t.nr_cap = 1;
-  {
-    int32_t *d_tlo, *d_thi;
-    ALLOC(d_tlo, int32_t, n_trow);
-    ALLOC(d_thi, int32_t, n_trow);
-    CK(cudaMemcpy(d_tlo, pc->tlo.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(d_thi, pc->thi.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
-    t.tlo = d_tlo;
-    t.thi = d_thi;
-  }
+  t.tlo = d_tlo;
+  t.thi = d_thi;
   CK(trsv_prepare(precision));
   st = set_schedule(pc, trsv_ctas_per_sm(precision), 1023, 0, 0);
   if (st != CPM_OK) return st;

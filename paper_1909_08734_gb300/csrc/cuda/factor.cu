@@ -700,6 +700,57 @@ cudaError_t launch_diag_inverse(const void* a, int fp64, const SubMeta* meta, in
   return cudaGetLastError();
 }
 
+// Chain tiles of the solves.  In tile row I the forward substitution computes
+//     x_I = Linv_I (b_I - sum_{J < I-1} L_IJ x_J) - (Linv_I L_{I,I-1}) x_{I-1}
+// and the backward one likewise with Uinv_I U_{I,I+1} x_{I+1}: the product with the inverse
+// is taken before the neighbouring row's piece arrives, which leaves one matrix-vector
+// product on the chain between consecutive tile rows.  This kernel replaces L_{I,I-1} by
+// Linv_I L_{I,I-1} and U_{I,I+1} by Uinv_I U_{I,I+1} in place (tiles inside the envelope
+// only; sums in FP64).
+template <typename T, typename C>
+__global__ void __launch_bounds__(64) chain_tiles_kernel(T* a, const SubMeta* __restrict__ meta, const C* inv,
+                                                        const int32_t* __restrict__ tlo,
+                                                        const int32_t* __restrict__ thi) {
+  const SubMeta m = meta[blockIdx.y];
+  const int I = blockIdx.x;
+  if (I >= m.T) return;
+  const int64_t trow = (m.row_off >> 6) + I;
+  __shared__ C X[64][65];
+  const int c = threadIdx.x;
+  for (int side = 0; side < 2; ++side) {
+    const int J = side == 0 ? I - 1 : I + 1;
+    if (side == 0 ? tlo[trow] > J : thi[trow] < J) continue;   // outside the envelope
+    const C* xi = inv + (trow * 2 + side) * (int64_t)TILE_ELEMS;
+    T* tb = a + tile_base(m, I, J);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 4096; e += 64) {
+      const int i = e & 63, j = e >> 6;
+      X[i][j] = xi[off_plain(i, j)];
+    }
+    double bc[64];                              // column c of the tile
+#pragma unroll
+    for (int k = 0; k < 64; ++k) bc[k] = (double)tb[Layout<T>::off(k, c)];
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < 64; ++r) {
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < 64; ++k) acc += (double)X[r][k] * bc[k];
+      tb[Layout<T>::off(r, c)] = (T)acc;
+    }
+  }
+}
+
+cudaError_t launch_chain_tiles(void* a, int fp64, const SubMeta* meta, int n_sub, int t_max, const void* inv,
+                               const int32_t* tlo, const int32_t* thi, cudaStream_t s) {
+  dim3 g(t_max, n_sub);
+  if (fp64)
+    chain_tiles_kernel<double, double><<<g, 64, 0, s>>>((double*)a, meta, (const double*)inv, tlo, thi);
+  else
+    chain_tiles_kernel<float, float><<<g, 64, 0, s>>>((float*)a, meta, (const float*)inv, tlo, thi);
+  return cudaGetLastError();
+}
+
 __global__ void pack_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ out,
                                  int64_t n_tiles) {
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {

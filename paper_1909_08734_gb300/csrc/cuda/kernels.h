@@ -96,6 +96,10 @@ cudaError_t launch_lu_finish(const FactorDev& f, const int32_t* unknowns, const 
                              const int32_t* own_flag, int32_t* gather, int32_t* scatter,
                              void* dinv, cudaStream_t s);
 cudaError_t launch_pack_bf16(const float* a, __nv_bfloat16* out, int64_t n_tiles, cudaStream_t s);
+// Replaces L_{I,I-1} by L_II^{-1} L_{I,I-1} and U_{I,I+1} by U_II^{-1} U_{I,I+1} in every tile
+// row whose envelope holds them (the solves' chain tiles); inv as from launch_diag_inverse.
+cudaError_t launch_chain_tiles(void* a, int fp64, const SubMeta* meta, int n_sub, int t_max, const void* inv,
+                               const int32_t* tlo, const int32_t* thi, cudaStream_t s);
 cudaError_t launch_diag_inverse(const void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
                                 void* inv, cudaStream_t s);
 

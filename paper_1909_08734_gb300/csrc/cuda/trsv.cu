@@ -184,14 +184,26 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
     unsigned char* dst = smem + (size_t)st * STAGE;
     mbar_expect_tx(&bar[st], STAGE);
     const SubMeta m = t.meta[e.j];
-    if (l < e.nq) {
-      const int q = e.q0 + l;
+    // load order of a diagonal item: off-diagonal tiles but the chain tile, the inverse
+    // pieces, the chain tile (the neighbouring row's, premultiplied by the inverse)
+    int tq = -1, piece = -1;
+    if (e.diag && e.nq > 0) {
+      if (l < e.nq - 1) tq = l;
+      else if (l < e.nq - 1 + PIECES) piece = l - (e.nq - 1);
+      else tq = e.nq - 1;
+    } else if (l < e.nq) {
+      tq = l;
+    } else {
+      piece = l - e.nq;
+    }
+    if (tq >= 0) {
+      const int q = e.q0 + tq;
       const int J = e.bwd ? e.jb - q : e.jb + q;
       bulk_g2s(dst, tiles + tile_base(m, e.I, J), STAGE, &bar[st]);
     } else {
       const int64_t trow = (m.row_off >> 6) + e.I;
       const unsigned char* it = (const unsigned char*)(inv + (trow * 2 + e.bwd) * (int64_t)TILE_ELEMS);
-      bulk_g2s(dst, it + (size_t)(l - e.nq) * STAGE, STAGE, &bar[st]);
+      bulk_g2s(dst, it + (size_t)piece * STAGE, STAGE, &bar[st]);
     }
     ++lc;
   };
@@ -254,27 +266,20 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
       return t.ytag + ((m.row_off + 64 * J + tid) * NR + q) * W;
     };
     auto pwords = [&](int seg, int q) { return t.ptag + (((trow * t.maxseg + seg) * 64 + tid) * NR + q) * W; };
+    // a diagonal item leaves its chain tile (the last one, next to the diagonal) for after
+    // the inverse product
+    const int nt = (e.diag && e.nq > 0) ? e.nq - 1 : e.nq;
     typename Tagged<C>::Raw pre[NR];
-    if (tid < 64 && e.nq > 0)
+    if (tid < 64 && nt > 0)
 #pragma unroll
       for (int q = 0; q < NR; ++q) pre[q] = Tagged<C>::load(ywords(0, q));
     C acc[NR], psum[NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q) acc[q] = psum[q] = (C)0;
-    for (int l = 0; l < e.nq; ++l) {
+    for (int l = 0; l < nt; ++l) {
       const bool staged = stage_ready(cc);
       bool ok = staged;
       if (tid < 64) {
-        // the last tile of a diagonal item waits for the chain; collect the partial sums
-        // of the other segments first (they are normally ready by then)
-        if (e.diag && l == e.nq - 1)
-          for (int sg = 0; sg < e.nseg - 1 && ok; ++sg)
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {
-              C v = (C)0;
-              if (ok) ok = poll_value<C>(pwords(sg, q), tag, &v, t.sync, t.status);
-              psum[q] += v;
-            }
         // the words were loaded one tile earlier; poll only if they were not yet published
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
           if (ok && !Tagged<C>::check(pre[q], tag, &v)) ok = poll_value<C>(ywords(l, q), tag, &v, t.sync, t.status);
           yb[l & 1][q][tid] = v;
         }
-        if (l + 1 < e.nq)
+        if (l + 1 < nt)
 #pragma unroll
           for (int q = 0; q < NR; ++q) pre[q] = Tagged<C>::load(ywords(l + 1, q));
       }
@@ -320,17 +325,32 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
 #pragma unroll
         for (int q = 0; q < NR; ++q) Tagged<C>::put(pwords(e.seg, q), red[q][tid] + red[q][tid + 64], tag);
     } else {
-      // diagonal block through its inverse: x = Inv (b - off-diagonal products)
+      // diagonal block through its inverse: c = Inv (b - products of the tiles before the
+      // chain tile); then x = c - (Inv L_{I,I-1}) x_{I-1} (backward: Uinv U_{I,I+1} x_{I+1})
 #pragma unroll
       for (int q = 0; q < NR; ++q) red[q][tid] = acc[q];
       bool ok = true;
       C own[NR];
 #pragma unroll
       for (int q = 0; q < NR; ++q) {
-        if (e.nq == 0) psum[q] = (C)0;  // no own tile (first row of a sweep): no partials
+        if (e.nq == 0) psum[q] = (C)0;  // no off-diagonal tile (first row of a sweep): no partials
         own[q] = rhs[q];
         if (e.bwd && tid < 64 && ok)
           ok = poll_value<C>(t.ytag + ((ro + tid) * NR + q) * W, tag_f, &own[q], t.sync, t.status);
+      }
+      // partial sums of the other segments (normally ready by now), then start loading the
+      // chain tile's solved piece
+      if (tid < 64) {
+        for (int sg = 0; sg < e.nseg - 1 && ok; ++sg)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            C v = (C)0;
+            if (ok) ok = poll_value<C>(pwords(sg, q), tag, &v, t.sync, t.status);
+            psum[q] += v;
+          }
+        if (e.nq > 0)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) pre[q] = Tagged<C>::load(ywords(e.nq - 1, q));
       }
       int staged = 0;
       for (int k = 0; k < PIECES && ok; ++k) {
@@ -365,16 +385,56 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
 #pragma unroll
       for (int q = 0; q < NR; ++q) red2[q][tid] = (p4[q][0] + p4[q][1]) + (p4[q][2] + p4[q][3]);
       __syncthreads();
+      C x[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) x[q] = red2[q][tid & 63] + red2[q][(tid & 63) + 64];
+      cc += PIECES;
+      if (e.nq > 0) {
+        if (tid == 0) pump();          // every thread is past the inverse: its stages are free
+        const bool sc = stage_ready(cc);
+        ok = sc;
+        if (tid < 64)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            C v = (C)0;
+            if (ok && !Tagged<C>::check(pre[q], tag, &v))
+              ok = poll_value<C>(ywords(e.nq - 1, q), tag, &v, t.sync, t.status);
+            yb[0][q][tid] = v;
+          }
+        if (!__syncthreads_and(ok)) {
+          bad = true;
+          if (tid == 0 && sc) cc++;
+          break;
+        }
+        const S* tile = (const S*)(smem + (size_t)(cc % NSTAGE) * STAGE);
+        C a4[NR][4];
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a4[q][u] = (C)0;
+#pragma unroll
+        for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 4)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const C a = (C)cvt(tile[Layout<S>::off(r, c0 + u)]);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) a4[q][u] += a * yb[0][q][c0 + u];
+          }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) red[q][tid] = (a4[q][0] + a4[q][1]) + (a4[q][2] + a4[q][3]);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NR; ++q) x[q] -= red[q][tid & 63] + red[q][(tid & 63) + 64];
+        cc++;
+      }
       if (tid < 64) {
         const int sidx = e.bwd ? t.scatter[ro + tid] : -1;
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
-          const C x = red2[q][tid] + red2[q][tid + 64];
-          Tagged<C>::put(t.ytag + ((ro + tid) * NR + q) * W, x, tag);
-          if (sidx >= 0) z_out.ptr(q)[sidx] = (double)x;
+          Tagged<C>::put(t.ytag + ((ro + tid) * NR + q) * W, x[q], tag);
+          if (sidx >= 0) z_out.ptr(q)[sidx] = (double)x[q];
         }
       }
-      cc += PIECES;
     }
     // advance: the next item becomes current, fetch a new next one, keep the ring full
     if (tid == 0) {
