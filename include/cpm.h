@@ -159,6 +159,20 @@ cpm_status cpm_local_coo(const cpm_band* band, const cpm_part* part, double c,
                          int transmission, double alpha, double alpha_x, int j, int64_t* n,
                          int64_t* nnz, int32_t* rows, int32_t* cols, double* vals);
 
+/* Order and tile envelope of local operator j as oras_setup factors it (host only, no GPU).
+ * Any symmetric permutation of the local unknowns leaves the local solves of Eq. algRAS
+ * unchanged up to rounding; oras_setup uses perm[new] = old, the reverse Cuthill-McKee order
+ * of the pattern of A_j + A_j^T (deterministic).  For the reordered matrix, padded to 64 T
+ * rows (T = ceil(n / 64), identity on the padding): first[r] / last[r] = the first / last
+ * nonzero 64-column tile of row r (64 T entries each); pend[s] (s < T) = one past the last row
+ * position that a row with first <= s can occupy at step s of an LU with partial pivoting
+ * (at least 64 (s + 1)): the rows the panel of step s must cover.  Call with perm == NULL to
+ * get *n and *T; then with arrays of n, 64 T, 64 T and T entries (caller-owned host memory).
+ * Errors: INVALID_ARG, STENCIL, OOM. */
+cpm_status cpm_local_order(const cpm_band* band, const cpm_part* part, double c, int transmission,
+                           double alpha, double alpha_x, int j, int64_t* n, int* T, int32_t* perm,
+                           int32_t* first, int32_t* last, int32_t* pend);
+
 /* Preconditioner setup (Sec. 5 local operators; "local operators" phase of Sec. 6.6):
  * uploads the band to the device, assembles every local matrix as a dense tile-major
  * matrix on the GPU, factors all of them with partial pivoting in batched launches and

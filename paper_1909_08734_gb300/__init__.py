@@ -219,6 +219,24 @@ def cpm_local_coo(band: Band, part: Partition, c: float, transmission: str, alph
     return n.value, rows, cols, vals
 
 
+def cpm_local_order(band: Band, part: Partition, c: float, transmission: str, alpha: float,
+                    alpha_x: float, j: int):
+    """(perm, first, last, pend) of local operator j: see include/cpm.h."""
+    lib = _capi.load()
+    n = C.c_int64()
+    T = C.c_int()
+    tr = TRANSMISSIONS[transmission]
+    args = (band.handle, part.handle, float(c), tr, float(alpha), float(alpha_x), int(j), C.byref(n), C.byref(T))
+    _check(lib.cpm_local_order(*args, None, None, None, None), "cpm_local_order")
+    perm = np.zeros(n.value, np.int32)
+    first = np.zeros(64 * T.value, np.int32)
+    last = np.zeros(64 * T.value, np.int32)
+    pend = np.zeros(T.value, np.int32)
+    _check(lib.cpm_local_order(*args, *(x.ctypes.data_as(C.c_void_p) for x in (perm, first, last, pend))),
+           "cpm_local_order")
+    return perm, first, last, pend
+
+
 def oras_setup(band: Band, part: Partition, c: float, transmission: str = "oras",
                alpha: float = 4.0, alpha_x: float = 40.0, precision: str = "fp64",
                stream=None, simt_lu: bool = False) -> Preconditioner:

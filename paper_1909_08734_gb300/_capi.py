@@ -84,6 +84,8 @@ _SIGS = {
     "cpm_partition_destroy": (None, [_P]),
     "cpm_local_coo": (C.c_int, [_P, _P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P, _P, _P]),
+    "cpm_local_order": (C.c_int, [_P, _P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_int), _P, _P, _P, _P]),
     "oras_setup": (C.c_int, [_P, _P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int, _P,
                              C.POINTER(_P)]),
     "oras_info_get": (C.c_int, [_P, C.POINTER(oras_info)]),

@@ -1,3 +1,4 @@
+#include <algorithm>
 // C ABI: host-only entry points (band, partition, local operators, status strings).
 #include <new>
 #include <string>
@@ -212,6 +213,41 @@ cpm_status cpm_local_coo(const cpm_band* band, const cpm_part* part, double c,
     return CPM_OK;
   } catch (const std::bad_alloc&) {
     cpm::set_error("cpm_local_coo: out of host memory");
+    return CPM_ERR_OOM;
+  }
+}
+
+cpm_status cpm_local_order(const cpm_band* band, const cpm_part* part, double c, int transmission,
+                           double alpha, double alpha_x, int j, int64_t* n, int* T, int32_t* perm,
+                           int32_t* first, int32_t* last, int32_t* pend) {
+  if (!band || !part || !n || !T) {
+    cpm::set_error("cpm_local_order: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  try {
+    cpm::LocalCOO L;
+    cpm_status st = cpm::build_local_coo(band->b, part->p, c, transmission, alpha, alpha_x, j, L);
+    if (st != CPM_OK) return st;
+    *n = L.n;
+    *T = (int)((L.n + 63) / 64);
+    if (!perm) return CPM_OK;
+    if (!first || !last || !pend) {
+      cpm::set_error("cpm_local_order: NULL output array");
+      return CPM_ERR_INVALID_ARG;
+    }
+    std::vector<int32_t> p, inv(L.n), f, l, pe;
+    cpm::rcm_order(L, p);
+    for (int64_t k = 0; k < L.n; ++k) inv[p[k]] = (int32_t)k;
+    for (auto& r : L.row) r = inv[r];
+    for (auto& cc : L.col) cc = inv[cc];
+    cpm::envelope(L, *T, f, l, pe);
+    std::copy(p.begin(), p.end(), perm);
+    std::copy(f.begin(), f.end(), first);
+    std::copy(l.begin(), l.end(), last);
+    std::copy(pe.begin(), pe.end(), pend);
+    return CPM_OK;
+  } catch (const std::bad_alloc&) {
+    cpm::set_error("cpm_local_order: out of host memory");
     return CPM_ERR_OOM;
   }
 }

@@ -161,3 +161,63 @@ def test_plan_is_host_only_and_consistent(pair):
     assert G.oras_plan(band, part, "oras", "fp32", 80, 1)["resident_bytes"] > plans["fp32"]["resident_bytes"]
     with pytest.raises(G.CpmError):
         G.oras_plan(band, part, "oras", "fp32", 0, 1)
+
+
+def _bandwidth(rows, cols):
+    return int(np.max(np.abs(rows.astype(np.int64) - cols)))
+
+
+@pytest.mark.parametrize("case", [("sphere", 1.0, 0.0, 0.1, 3, 4, 2, "oras"),
+                                  ("torus", 1.0, 0.4, 0.05, 3, 16, 2, "ras")])
+def test_local_order_and_tile_envelope(case):
+    """The reverse Cuthill-McKee order is a permutation that narrows the local matrix, and the
+    tile envelope holds for an LU with partial pivoting: with the pivots SciPy's dense LU
+    chooses, every pivot lies in the panel's row range and every entry of L and U outside the
+    tracked envelope is exactly zero (the tracking rule restated from the envelope's
+    definition: interchanges move (first, last) with the row; a step raises last to the pivot
+    block's largest last for every row below it with first <= s)."""
+    import scipy.linalg as sla
+    kind, R, r, h, p, ns, no, tr = case
+    band = G.cpm_build_band(kind, R, r, h, p)
+    part = G.cpm_partition(band, ns, None, no)
+    for j in range(0, ns, 5):
+        n, rows, cols, vals = G.cpm_local_coo(band, part, 2.0, tr, 4.0, 40.0, j)
+        perm, first, last, pend = G.cpm_local_order(band, part, 2.0, tr, 4.0, 40.0, j)
+        assert np.array_equal(np.sort(perm), np.arange(n))
+        inv = np.empty(n, np.int64)
+        inv[perm] = np.arange(n)
+        pr, pc = inv[rows], inv[cols]
+        assert _bandwidth(pr, pc) < _bandwidth(rows, cols)
+        T = (n + 63) // 64
+        NP = 64 * T
+        # first / last / pend from the definitions
+        f = np.arange(NP) // 64
+        lst = f.copy()
+        np.minimum.at(f, pr, pc // 64)
+        np.maximum.at(lst, pr, pc // 64)
+        assert np.array_equal(first, f) and np.array_equal(last, lst)
+        for s in range(T):
+            below = np.nonzero(f <= s)[0]
+            assert pend[s] == min(NP, max(below.max() + 1, 64 * (s + 1)))
+        # dense LU with partial pivoting of the reordered, padded matrix
+        A = np.eye(NP)
+        A[:n, :n] = 0.0
+        np.add.at(A, (pr, pc), vals)
+        lu, piv = sla.lu_factor(A, check_finite=False)
+        F, Lt = first.astype(np.int64).copy(), last.astype(np.int64).copy()
+        for s in range(T):
+            k0 = 64 * s
+            for c in range(64):
+                q = piv[k0 + c]
+                assert k0 + c <= q < pend[s]
+                F[[k0 + c, q]] = F[[q, k0 + c]]
+                Lt[[k0 + c, q]] = Lt[[q, k0 + c]]
+            hu = max(s, Lt[k0:k0 + 64].max())
+            sel = np.arange(k0 + 64, pend[s])
+            sel = sel[F[sel] <= s]
+            Lt[sel] = np.maximum(Lt[sel], hu)
+        for I in range(T):
+            lo, hi = F[64 * I:64 * I + 64].min(), min(T - 1, Lt[64 * I:64 * I + 64].max())
+            blk = lu[64 * I:64 * I + 64]
+            assert not np.any(blk[:, :64 * lo]), (j, I, lo)
+            assert not np.any(blk[:, 64 * (hi + 1):]), (j, I, hi)
