@@ -28,8 +28,8 @@ struct Graph {
   int32_t deg(int32_t v) const { return (int32_t)(ptr[v + 1] - ptr[v]); }
 };
 
-// symmetric pattern without the diagonal, neighbours sorted by (degree, index); built by
-// counting (both directions of every off-diagonal entry) and per-row deduplication
+// symmetric pattern without the diagonal; built by counting (both directions of every
+// off-diagonal entry) and per-row deduplication
 Graph pattern(const LocalCOO& L) {
   const int64_t n = L.n;
   Graph g;
@@ -60,10 +60,6 @@ Graph pattern(const LocalCOO& L) {
     }
     g.ptr[v + 1] = (int64_t)g.adj.size();
   }
-  for (int64_t v = 0; v < n; ++v)
-    std::sort(g.adj.begin() + g.ptr[v], g.adj.begin() + g.ptr[v + 1], [&](int32_t a, int32_t b) {
-      return g.deg(a) != g.deg(b) ? g.deg(a) < g.deg(b) : a < b;
-    });
   return g;
 }
 
@@ -124,12 +120,14 @@ void rcm_order(const LocalCOO& L, std::vector<int32_t>& perm) {
       depth = d2;
       last.swap(l2);
     }
-    // Cuthill-McKee sweep of the component
+    // Cuthill-McKee sweep of the component: the unvisited neighbours of each vertex in the
+    // order of (degree, index)
     const size_t start = perm.size();
     perm.push_back(root);
     done[root] = 1;
     for (size_t h = start; h < perm.size(); ++h) {
       const int32_t v = perm[h];
+      const size_t first_new = perm.size();
       for (int64_t k = g.ptr[v]; k < g.ptr[v + 1]; ++k) {
         const int32_t w = g.adj[k];
         if (!done[w]) {
@@ -137,6 +135,9 @@ void rcm_order(const LocalCOO& L, std::vector<int32_t>& perm) {
           perm.push_back(w);
         }
       }
+      std::sort(perm.begin() + first_new, perm.end(), [&](int32_t a, int32_t b) {
+        return g.deg(a) != g.deg(b) ? g.deg(a) < g.deg(b) : a < b;
+      });
     }
     std::reverse(perm.begin() + start, perm.end());
   }
