@@ -216,7 +216,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
 #pragma omp parallel for schedule(dynamic, 1)
   for (int j = 0; j < ns; ++j) {
     try {
-      sts[j] = cpm::build_local_coo(B, P, c, transmission, alpha, alpha_x, j, coo[j]);
+      sts[j] = cpm::build_local_coo(B, P, c, transmission, alpha, alpha_x, j, coo[j], false);
       if (sts[j] != CPM_OK) errs[j] = cpm_last_error();
     } catch (const std::bad_alloc&) {
       sts[j] = CPM_ERR_OOM;

@@ -118,8 +118,11 @@ cpm_status build_band_algorithmic(const Surface& s, double h, int p, Band& out);
 void band_release_device(Band& b);
 cpm_status build_partition(const Band& band, int n_sub, const int64_t* weights, int n_overlap,
                            int align_passes, Partition& out);
+// Local operator of subdomain j, duplicates summed; sorted_rows: entries of a row in column
+// order (otherwise in first-touch order; the values are the same either way).
 cpm_status build_local_coo(const Band& band, const Partition& part, double c, int transmission,
-                           double alpha, double alpha_x, int j, LocalCOO& out);
+                           double alpha, double alpha_x, int j, LocalCOO& out,
+                           bool sorted_rows = true);
 
 }  // namespace cpm
 

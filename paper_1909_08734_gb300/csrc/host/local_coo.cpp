@@ -48,7 +48,7 @@ bool ext_row(const Band& B, const double y[3], double scale, const std::vector<i
 }  // namespace
 
 cpm_status build_local_coo(const Band& B, const Partition& part, double c, int transmission,
-                           double alpha, double alpha_x, int j, LocalCOO& out) {
+                           double alpha, double alpha_x, int j, LocalCOO& out, bool sorted_rows) {
   if (j < 0 || j >= part.n_sub || part.band != &B) {
     set_error("local operator: bad subdomain index or band/partition mismatch");
     return CPM_ERR_INVALID_ARG;
@@ -143,6 +143,13 @@ cpm_status build_local_coo(const Band& B, const Partition& part, double c, int t
   std::vector<double> acc(n, 0.0);
   std::vector<uint8_t> hit(n, 0);
   std::vector<int32_t> touched;
+  {
+    // entries per row: about (p+1)^3 distinct columns from 6 overlapping stencils
+    const size_t guess = (size_t)n * (size_t)(3 * B.P() * B.P() * B.P() / 2);
+    out.row.reserve(guess);
+    out.col.reserve(guess);
+    out.val.reserve(guess);
+  }
   const int64_t n_pde = (ras || r1) ? n : (int64_t)S.sigma.size();
   for (int64_t i = 0; i < n; ++i) {
     touched.clear();
@@ -176,7 +183,9 @@ cpm_status build_local_coo(const Band& B, const Partition& part, double c, int t
       const Row& r = rows[pos[g]];
       for (int e = 0; e < r.n; ++e) put(r.col[e], -(6.0 * invh2) * r.w[e]);
     }
-    std::sort(touched.begin(), touched.end());
+    // the value of every entry is summed in a fixed order either way; sorting only orders
+    // the output (set-up consumes the entries in any order)
+    if (sorted_rows) std::sort(touched.begin(), touched.end());
     for (int32_t col : touched) {
       out.row.push_back((int32_t)i);
       out.col.push_back(col);
