@@ -5,11 +5,14 @@
 //   prolong : z[g] = z_j[loc(g)] for g in the disjoint set of j (restricted partition of
 //             unity, Eq. restCons), so every global entry is written exactly once.
 //
-// Work items.  Tile row I of subdomain j needs p = I (forward) or T-1-I (backward)
-// off-diagonal 64x64 tiles.  They are split into segments of at most kseg tiles: every
-// segment but the last is a "partial" item that publishes the partial product of its tiles
-// with the solved pieces; the last segment is the "diagonal" item, which adds the partials,
-// applies the precomputed inverse of the diagonal block and publishes the solved piece of
+// Work items.  Tile row I of subdomain j needs the off-diagonal 64x64 tiles inside the
+// factors' tile envelope: L tiles tlo..I-1 (forward), U tiles I+1..thi (backward); the tiles
+// outside are exactly zero and are never read.  They are split into segments of at most kseg
+// tiles: every segment but the last is a "partial" item that publishes the partial product of
+// its tiles with the solved pieces; the last segment is the "diagonal" item, which adds the
+// partials, applies the precomputed inverse of the diagonal block and then the chain tile
+// (the tile next to the diagonal, stored premultiplied by that inverse, so only one
+// matrix-vector product waits for the neighbouring row), and publishes the solved piece of
 // row I.  Items are queued forward-then-backward, each direction sorted by the chain
 // position they wait for.
 //
