@@ -174,9 +174,9 @@ cpm_status cpm_local_order(const cpm_band* band, const cpm_part* part, double c,
                            int32_t* first, int32_t* last, int32_t* pend);
 
 /* Preconditioner setup (Sec. 5 local operators; "local operators" phase of Sec. 6.6):
- * uploads the band to the device, assembles every local matrix as a dense tile-major
- * matrix on the GPU, factors all of them with partial pivoting in batched launches and
- * keeps the factors resident.  CPM_FP64: FP64 throughout.  CPM_FP32: FP32 factors, trailing
+ * uploads the band to the device, orders every local matrix's unknowns (cpm_local_order),
+ * assembles it tile-major on the GPU, factors all of them with partial pivoting in batched
+ * launches over the tiles of their envelope and keeps the factors resident.  CPM_FP64: FP64 throughout.  CPM_FP32: FP32 factors, trailing
  * updates on the tensor cores with split-tf32 operands (FP32 accuracy).  CPM_BF16: trailing
  * updates with bf16 operands and FP32 accumulation, factors stored in BF16 for the solves.
  * Synchronises the stream.

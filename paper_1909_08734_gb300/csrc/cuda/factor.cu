@@ -1,14 +1,18 @@
-// Batched dense LU with partial pivoting of all local matrices A_j (Sec. 5: the local
-// problems are solved by LU factorisation).  Every A_j is padded to 64 T_j with an
-// identity block and stored as 64 x 64 tiles; one blocked right-looking step per tile
-// column s runs over all subdomains at once:
-//   panel  : factor tile column s (rows >= 64 s) column by column, pivoting on max |a|
-//   swap   : apply the panel's row interchanges to every other tile column
-//   trsm   : U_sJ = L_ss^{-1} A_sJ for J > s
-//   update : A_IJ -= L_Is U_sJ for I, J > s   (the dense contraction; SIMT here, the
-//            tensor-core version lives in lu_tc.cu)
-// FP64 mode keeps double tiles; FP32 and BF16 modes keep float tiles in the swizzled
-// layout of common.cuh.
+// Batched LU with partial pivoting of all local matrices A_j (Sec. 5: the local problems
+// are solved by LU factorisation).  Every A_j (unknowns in reverse Cuthill-McKee order) is
+// padded to 64 T_j with an identity block and stored as 64 x 64 tiles; one blocked
+// right-looking step per tile column s runs over all subdomains at once:
+//   panel    : factor tile column s column by column, pivoting on max |a|, over the rows
+//              that can be nonzero in it (below pend[s])
+//   envelope : move (first, last) with the interchanges, take the U row's extent hiu, and
+//              raise last to hiu for the rows the step updates
+//   swap     : apply the panel's row interchanges to every other tile column
+//   trsm     : U_sJ = L_ss^{-1} A_sJ for s < J <= hiu
+//   update   : A_IJ -= L_Is U_sJ for the tiles inside the envelope (SIMT here, the
+//              tensor-core versions live in lu_tc.cu)
+// Tiles outside the envelope are zero and stay zero (the host-side rules are in
+// host/ordering.cpp).  FP64 mode keeps double tiles; FP32 and BF16 modes keep float tiles in
+// the swizzled layout of common.cuh.
 #include <algorithm>
 #include <cooperative_groups.h>
 
