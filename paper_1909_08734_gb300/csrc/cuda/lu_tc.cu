@@ -25,9 +25,7 @@
 
 namespace cpmdev {
 
-// threads of lu_update_tc_kernel (the lock-step kernel, used for bf16: two CTAs per SM); with
-// split tf32 it measured best at 16 warps, but the warp-specialised kernel below replaced it
-template <int KIND> __host__ __device__ constexpr int tc_threads() { return KIND == 2 ? 512 : 256; }
+constexpr int TC_LS_THREADS = 256;       // lock-step bf16 kernel: 8 warps, two CTAs per SM
 constexpr int TC_TMEM_COLS = 64;         // FP32 accumulator columns per buffer (two buffers)
 
 // ---- tcgen05 / descriptor helpers -------------------------------------------------------
@@ -207,14 +205,18 @@ __global__ void __launch_bounds__(256) lu_split_u_kernel(const float* __restrict
   }
 }
 
+// Lock-step bf16 update (KIND 1): every column passes two CTA barriers; thread 0 waits for
+// the U tile and issues the MMAs, all threads run the epilogue.  (The split-tf32 update runs
+// in the warp-specialised kernel further down.)
 template <int KIND>
-__global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float* a, const SubMeta* __restrict__ meta,
+__global__ void __launch_bounds__(TC_LS_THREADS) lu_update_tc_kernel(float* a, const SubMeta* __restrict__ meta,
                                                                    const unsigned char* __restrict__ ubuf, int s,
                                                                    int jchunk, int* status,
                                                                    const int32_t* __restrict__ pend,
                                                                    const int32_t* __restrict__ hiu, int t_max) {
+  static_assert(KIND == 1, "the lock-step kernel is the bf16 update");
   using L = TcSmem<KIND>;
-  constexpr int TC_THREADS = tc_threads<KIND>();
+  constexpr int TC_THREADS = TC_LS_THREADS;
   constexpr int TC_CG = TC_THREADS / 128;      // epilogue column groups (warps per lane quarter)
   constexpr int TC_CW = 64 / TC_CG;            // accumulator columns per warp in the epilogue
   const SubMeta m = meta[blockIdx.z];
@@ -284,17 +286,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float*
     if (!two)
       for (int e = tid; e < TILE_ELEMS; e += TC_THREADS) rawA[TILE_ELEMS + e] = 0.0f;
     __syncthreads();
-    if (KIND == 2) {                            // A hi / lo, rewritten K-major
-      unsigned char* ahi = base + TcSmem<2>::A_HI;
-      unsigned char* alo = base + TcSmem<2>::A_LO;
-      for (int e = tid; e < 2 * TILE_ELEMS; e += TC_THREADS) {
-        const int t = e >> 12, el = e & 4095, i = el & 63, k = el >> 6;
-        const float x = rawA[t * TILE_ELEMS + off_sw32(i, k)], hi = tf32_round(x);
-        const uint32_t o = tf32_a_off(64 * t + i, k);
-        *(float*)(ahi + o) = hi;
-        *(float*)(alo + o) = tf32_round(x - hi);
-      }
-    } else {
+    {                                           // A pair to bf16, rewritten K-major
       unsigned char* abf = base + TcSmem<1>::A_BF;
       for (int e = tid; e < 2 * TILE_ELEMS; e += TC_THREADS) {
         const int t = e >> 12, el = e & 4095, i = el & 63, k = el >> 6;
@@ -333,19 +325,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float*
         const uint32_t d_tmem = taddr + (uint32_t)(b * TC_TMEM_COLS);
         // a descriptor's start-address field holds addr >> 4: an offset adds (off >> 4)
         const uint64_t db = smem_desc(smem_u32(stage_b(bs)), 16, 1024);
-        if (KIND == 2) {
-          constexpr uint32_t idesc = instr_desc(2);
-          const uint64_t dhi = smem_desc(smem_u32(base) + TcSmem<2>::A_HI, 16, 1024);
-          const uint64_t dlo = smem_desc(smem_u32(base) + TcSmem<2>::A_LO, 16, 1024);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {         // K = 8 tf32 values (32 bytes) per instruction
-            const uint64_t ka = ((k >> 2) * 16384 + (k & 3) * 32) >> 4;
-            const uint64_t kb = ((k >> 2) * 8192 + (k & 3) * 32) >> 4;
-            mma<2>(d_tmem, dhi + ka, db + kb, idesc, k > 0 ? 1u : 0u);
-            mma<2>(d_tmem, dhi + ka, db + (16384 >> 4) + kb, idesc, 1u);
-            mma<2>(d_tmem, dlo + ka, db + kb, idesc, 1u);
-          }
-        } else {
+        {
           constexpr uint32_t idesc = instr_desc(1);
           const uint64_t da = smem_desc(smem_u32(base) + TcSmem<1>::A_BF, 16, 1024);
 #pragma unroll
@@ -382,7 +362,6 @@ __global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float*
       // element (lr, TC_CW colg + q) of a tile sits at row_base + (q >> 3) * 256 + v[q & 7]
       const int row_base = ((lr >> 5) * 8 + (TC_CW / 8) * colg) * 256 + (lr & 3);
       float* cs = stage_c(cp) + (row < 64 ? 0 : TILE_ELEMS) + row_base;
-      float* ct = a + tile_base(m, row < 64 ? I0 : I1, Jbeg + p) + row_base;
       float d[TC_CW];
       const uint32_t tcol = taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(bp * TC_TMEM_COLS + TC_CW * colg);
       if constexpr (TC_CW == 32) tmem_ld32(tcol, d);
@@ -391,28 +370,22 @@ __global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float*
 #pragma unroll
         for (int q = 0; q < TC_CW; ++q) {
           const int o = (q >> 3) * 256 + v_line[q & 7];
-          if constexpr (KIND == 1) cs[o] = cs[o] - d[q];    // stored by a bulk copy
-          else ct[o] = cs[o] - d[q];
+          cs[o] = cs[o] - d[q];                 // in place: stored by a bulk copy
         }
       }
       fence_before_sync();
       fence_proxy_async();
       __syncthreads();                          // accumulator buffer and C stage read
-      if constexpr (KIND == 1) {
-        // bf16: the updated tile pair leaves by a bulk copy from the C stage, which is refilled
-        // once that copy has read it (measured faster than per-thread stores; with split tf32,
-        // whose MMAs thread 0 also issues, per-thread stores measured faster)
-        if (tid == 0) {
-          bulk_s2g(a + tile_base(m, I0, Jbeg + p), stage_c(cp), 16384);
-          if (two) bulk_s2g(a + tile_base(m, I1, Jbeg + p), stage_c(cp) + TILE_ELEMS, 16384);
-          bulk_commit();
-          if (p + NC < nJ) {
-            bulk_wait_read_all();
-            issue_c(cp, Jbeg + p + NC);
-          }
+      // the updated tile pair leaves by a bulk copy from the C stage, which is refilled once
+      // that copy has read it (measured faster than per-thread stores here)
+      if (tid == 0) {
+        bulk_s2g(a + tile_base(m, I0, Jbeg + p), stage_c(cp), 16384);
+        if (two) bulk_s2g(a + tile_base(m, I1, Jbeg + p), stage_c(cp) + TILE_ELEMS, 16384);
+        bulk_commit();
+        if (p + NC < nJ) {
+          bulk_wait_read_all();
+          issue_c(cp, Jbeg + p + NC);
         }
-      } else if (tid == 0 && p + NC < nJ) {
-        issue_c(cp, Jbeg + p + NC);
       }
     }
   }
@@ -427,7 +400,7 @@ __global__ void __launch_bounds__(tc_threads<KIND>()) lu_update_tc_kernel(float*
     for (int b = 0; b < NC; ++b)
       for (; nc_wait[b] < nc_iss[b]; ++nc_wait[b]) mbar_wait_bounded(&bar_c[b], (uint32_t)nc_wait[b] & 1);
   }
-  if (KIND == 1 && tid == 0) bulk_wait_all();   // bulk stores complete before the CTA exits
+  if (tid == 0) bulk_wait_all();                // bulk stores complete before the CTA exits
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(taddr, 2 * TC_TMEM_COLS);
@@ -687,7 +660,7 @@ cudaError_t launch_lu_update_tc(const FactorDev& f, int step, int bf16, cudaStre
   unsigned char* ub = (unsigned char*)f.ubuf;
   if (bf16) {
     lu_split_u_kernel<1><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub, f.hiu);
-    lu_update_tc_kernel<1><<<g, tc_threads<1>(), 1024 + TcSmem<1>::TOTAL, s>>>(
+    lu_update_tc_kernel<1><<<g, TC_LS_THREADS, 1024 + TcSmem<1>::TOTAL, s>>>(
         (float*)f.a, f.meta, ub, step, jchunk, f.status, f.pend, f.hiu, f.t_max);
   } else {
     lu_split_u_kernel<2><<<gs, 256, 0, s>>>((const float*)f.a, f.meta, step, ub, f.hiu);
