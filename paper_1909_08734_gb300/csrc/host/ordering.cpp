@@ -13,6 +13,7 @@
 //   * rows with first <= s occupy positions below max{r : first_r <= s} at every step: a row
 //     moves down only into the old position of a pivot row of an earlier step.
 #include <algorithm>
+#include <memory>
 #include <numeric>
 #include <vector>
 
@@ -40,7 +41,7 @@ Graph pattern(const LocalCOO& L) {
       cnt[L.col[k] + 1]++;
     }
   for (int64_t v = 0; v < n; ++v) cnt[v + 1] += cnt[v];
-  std::vector<int32_t> raw(cnt[n]);
+  std::unique_ptr<int32_t[]> raw(new int32_t[cnt[n]]);   // every slot is written below
   std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
   for (size_t k = 0; k < L.row.size(); ++k)
     if (L.row[k] != L.col[k]) {
@@ -48,7 +49,7 @@ Graph pattern(const LocalCOO& L) {
       raw[pos[L.col[k]]++] = L.row[k];
     }
   g.ptr.assign(n + 1, 0);
-  g.adj.reserve(raw.size() / 2);
+  g.adj.reserve(cnt[n]);
   std::vector<int32_t> stamp(n, -1);
   for (int64_t v = 0; v < n; ++v) {
     for (int64_t k = cnt[v]; k < cnt[v + 1]; ++k) {
