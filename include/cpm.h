@@ -148,6 +148,22 @@ cpm_status cpm_partition_set(const cpm_part* part, int j, int which, const int32
                              int64_t* len);
 cpm_status cpm_partition_cross_points(const cpm_part* part, const int32_t** data,
                                       int64_t* len);
+/* Partition from caller-supplied labels (the paper partitions with a graph partitioner,
+ * Sec. 3.1; any labelling can be brought in): labels[g] in [0, n_sub) for every active node g
+ * (host, N_A entries, copied).  The overlap, boundary sets, generators and cross points follow
+ * from the labels exactly as in cpm_partition (Sec. 4.1, Sec. 4.2, Sec. 5.2.2).
+ * Errors: INVALID_ARG (label outside [0, n_sub), empty subdomain), STENCIL, OOM. */
+cpm_status cpm_partition_from_labels(const cpm_band* band, int n_sub, const int32_t* labels,
+                                     int n_overlap, cpm_part** out);
+/* Checkpoint of a partition (no counterpart in the paper): cpm_partition_save writes the
+ * labels with n_sub, N_O and a fingerprint of the band (N_A, N_A + N_G, h, p and a 64-bit
+ * FNV-1a hash of every node's integer grid coordinates) to the file at path (binary,
+ * little-endian); cpm_partition_load rebuilds the partition on a band with the same
+ * fingerprint through cpm_partition_from_labels, so the sets come out identical.
+ * Errors: INVALID_ARG (file cannot be opened, written or read, not a partition file, other
+ * band), STENCIL, OOM. */
+cpm_status cpm_partition_save(const cpm_part* part, const char* path);
+cpm_status cpm_partition_load(const cpm_band* band, const char* path, cpm_part** out);
 void cpm_partition_destroy(cpm_part* part);
 
 /* Local operator of subdomain j in coordinate form (host only, no GPU).  Local unknowns are

@@ -9,6 +9,7 @@ the GPU; the first call loads ``libcpm_gb300.so`` and raises if it has not been 
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -199,6 +200,29 @@ def cpm_partition(band: Band, n_sub: int, leaf_weights=None, n_overlap: int = 2,
     _check(lib.cpm_partition(band.handle, int(n_sub), wptr, int(n_overlap), int(align_passes),
                              C.byref(h_out)), "cpm_partition")
     return Partition(h_out, band, n_sub)
+
+
+def cpm_partition_from_labels(band: Band, labels, n_overlap: int = 2, n_sub: int | None = None) -> Partition:
+    """Partition from caller-supplied labels (one per active node, in [0, n_sub))."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    if n_sub is None:
+        n_sub = int(lab.max()) + 1 if lab.size else 0
+    h_out = C.c_void_p()
+    _check(_capi.load().cpm_partition_from_labels(band.handle, int(n_sub), lab.ctypes.data_as(C.c_void_p),
+                                                  int(n_overlap), C.byref(h_out)), "cpm_partition_from_labels")
+    return Partition(h_out, band, int(n_sub))
+
+
+def cpm_partition_save(part: Partition, path: str) -> None:
+    _check(_capi.load().cpm_partition_save(part.handle, os.fsencode(path)), "cpm_partition_save")
+
+
+def cpm_partition_load(band: Band, path: str) -> Partition:
+    h_out = C.c_void_p()
+    _check(_capi.load().cpm_partition_load(band.handle, os.fsencode(path), C.byref(h_out)), "cpm_partition_load")
+    p = Partition(h_out, band, 0)
+    p.n_sub = int(p.labels().max()) + 1       # every subdomain is non-empty
+    return p
 
 
 def cpm_local_coo(band: Band, part: Partition, c: float, transmission: str, alpha: float,

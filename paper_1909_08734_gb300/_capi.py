@@ -82,6 +82,9 @@ _SIGS = {
                                     C.POINTER(C.c_int64)]),
     "cpm_partition_cross_points": (C.c_int, [_P, C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.c_int64)]),
     "cpm_partition_destroy": (None, [_P]),
+    "cpm_partition_from_labels": (C.c_int, [_P, C.c_int, _P, C.c_int, C.POINTER(_P)]),
+    "cpm_partition_save": (C.c_int, [_P, C.c_char_p]),
+    "cpm_partition_load": (C.c_int, [_P, C.c_char_p, C.POINTER(_P)]),
     "cpm_local_coo": (C.c_int, [_P, _P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64), _P, _P, _P]),
     "cpm_local_order": (C.c_int, [_P, _P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,

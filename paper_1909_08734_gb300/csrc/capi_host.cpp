@@ -1,5 +1,7 @@
-#include <algorithm>
 // C ABI: host-only entry points (band, partition, local operators, status strings).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
 #include <new>
 #include <string>
 
@@ -136,6 +138,132 @@ cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_we
     cpm::set_error("cpm_partition: out of host memory");
     return CPM_ERR_OOM;
   }
+}
+
+cpm_status cpm_partition_from_labels(const cpm_band* band, int n_sub, const int32_t* labels,
+                                     int n_overlap, cpm_part** out) {
+  if (!band || !labels || !out) {
+    cpm::set_error("cpm_partition_from_labels: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  try {
+    cpm_part* p = new cpm_part();
+    cpm_status st = cpm::build_partition_from_labels(band->b, n_sub, labels, n_overlap, p->p);
+    if (st != CPM_OK) {
+      delete p;
+      return st;
+    }
+    *out = p;
+    return CPM_OK;
+  } catch (const std::bad_alloc&) {
+    cpm::set_error("cpm_partition_from_labels: out of host memory");
+    return CPM_ERR_OOM;
+  }
+}
+
+namespace {
+
+// partition file: header, then N_A int32 labels
+struct PartFileHeader {
+  char magic[8];              // "CPMPART1"
+  uint32_t version;           // 1
+  int32_t n_sub, n_overlap, p;
+  int64_t n_active, n_nodes;
+  double h;
+  uint64_t grid_hash;         // FNV-1a over the int32 grid coordinates of every node
+};
+
+uint64_t grid_hash(const cpm::Band& B) {
+  uint64_t x = 1469598103934665603ull;
+  const unsigned char* b = (const unsigned char*)B.ijk.data();
+  const size_t n = B.ijk.size() * sizeof(int32_t);
+  for (size_t k = 0; k < n; ++k) {
+    x ^= b[k];
+    x *= 1099511628211ull;
+  }
+  return x;
+}
+
+PartFileHeader header_of(const cpm::Band& B, int n_sub, int n_overlap) {
+  PartFileHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "CPMPART1", 8);
+  h.version = 1;
+  h.n_sub = n_sub;
+  h.n_overlap = n_overlap;
+  h.p = B.p;
+  h.n_active = B.n_active;
+  h.n_nodes = B.n_nodes();
+  h.h = B.h;
+  h.grid_hash = grid_hash(B);
+  return h;
+}
+
+}  // namespace
+
+cpm_status cpm_partition_save(const cpm_part* part, const char* path) {
+  if (!part || !path || !part->p.band) {
+    cpm::set_error("cpm_partition_save: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  const cpm::Partition& P = part->p;
+  const PartFileHeader h = header_of(*P.band, P.n_sub, P.n_overlap);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    cpm::set_error(std::string("cpm_partition_save: cannot open ") + path);
+    return CPM_ERR_INVALID_ARG;
+  }
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+            std::fwrite(P.labels.data(), sizeof(int32_t), P.labels.size(), f) == P.labels.size();
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) {
+    cpm::set_error(std::string("cpm_partition_save: write failed: ") + path);
+    return CPM_ERR_INVALID_ARG;
+  }
+  return CPM_OK;
+}
+
+cpm_status cpm_partition_load(const cpm_band* band, const char* path, cpm_part** out) {
+  if (!band || !path || !out) {
+    cpm::set_error("cpm_partition_load: NULL argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    cpm::set_error(std::string("cpm_partition_load: cannot open ") + path);
+    return CPM_ERR_INVALID_ARG;
+  }
+  PartFileHeader h;
+  const bool got = std::fread(&h, sizeof(h), 1, f) == 1;
+  if (!got || std::memcmp(h.magic, "CPMPART1", 8) != 0 || h.version != 1) {
+    std::fclose(f);
+    cpm::set_error(std::string("cpm_partition_load: not a partition file: ") + path);
+    return CPM_ERR_INVALID_ARG;
+  }
+  const PartFileHeader mine = header_of(band->b, h.n_sub, h.n_overlap);
+  if (h.p != mine.p || h.n_active != mine.n_active || h.n_nodes != mine.n_nodes || h.h != mine.h ||
+      h.grid_hash != mine.grid_hash) {
+    std::fclose(f);
+    cpm::set_error("cpm_partition_load: the file belongs to another band");
+    return CPM_ERR_INVALID_ARG;
+  }
+  std::vector<int32_t> labels;
+  try {
+    labels.resize((size_t)h.n_active);
+  } catch (const std::bad_alloc&) {
+    std::fclose(f);
+    cpm::set_error("cpm_partition_load: out of host memory");
+    return CPM_ERR_OOM;
+  }
+  const bool full = std::fread(labels.data(), sizeof(int32_t), labels.size(), f) == labels.size();
+  std::fclose(f);
+  if (!full) {
+    cpm::set_error(std::string("cpm_partition_load: truncated file: ") + path);
+    return CPM_ERR_INVALID_ARG;
+  }
+  return cpm_partition_from_labels(band, h.n_sub, labels.data(), h.n_overlap, out);
 }
 
 cpm_status cpm_partition_labels(const cpm_part* part, const int32_t** labels) {

@@ -118,6 +118,9 @@ cpm_status build_band_algorithmic(const Surface& s, double h, int p, Band& out);
 void band_release_device(Band& b);
 cpm_status build_partition(const Band& band, int n_sub, const int64_t* weights, int n_overlap,
                            int align_passes, Partition& out);
+// The same sets from caller-supplied labels (every label in [0, n_sub), no subdomain empty).
+cpm_status build_partition_from_labels(const Band& band, int n_sub, const int32_t* labels, int n_overlap,
+                                       Partition& out);
 // Local operator of subdomain j, duplicates summed; sorted_rows: entries of a row in column
 // order (otherwise in first-touch order; the values are the same either way).
 cpm_status build_local_coo(const Band& band, const Partition& part, double c, int transmission,

@@ -102,6 +102,8 @@ static void align_interfaces(const Band& B, int passes, std::vector<int32_t>& la
   }
 }
 
+static cpm_status finish_partition(const Band& B, Partition& part);
+
 cpm_status build_partition(const Band& B, int n_sub, const int64_t* weights, int n_overlap,
                            int align_passes, Partition& part) {
   if (n_sub < 1 || n_overlap < 0 || n_sub > B.n_active) {
@@ -117,7 +119,7 @@ cpm_status build_partition(const Band& B, int n_sub, const int64_t* weights, int
       }
       w[l] = weights[l];
     }
-  const int64_t na = B.n_active, N = B.n_nodes();
+  const int64_t na = B.n_active;
   part = Partition();
   part.band = &B;
   part.n_sub = n_sub;
@@ -125,6 +127,34 @@ cpm_status build_partition(const Band& B, int n_sub, const int64_t* weights, int
   part.labels.assign(na, -1);
   rcb(B, w, part.labels);
   if (align_passes > 0) align_interfaces(B, align_passes, part.labels);
+  return finish_partition(B, part);
+}
+
+cpm_status build_partition_from_labels(const Band& B, int n_sub, const int32_t* labels, int n_overlap,
+                                       Partition& part) {
+  if (n_sub < 1 || n_overlap < 0 || n_sub > B.n_active || !labels) {
+    set_error("cpm_partition_from_labels: need 1 <= n_sub <= N_A, n_overlap >= 0 and labels");
+    return CPM_ERR_INVALID_ARG;
+  }
+  const int64_t na = B.n_active;
+  for (int64_t g = 0; g < na; ++g)
+    if (labels[g] < 0 || labels[g] >= n_sub) {
+      set_error("cpm_partition_from_labels: a label is outside [0, n_sub)");
+      return CPM_ERR_INVALID_ARG;
+    }
+  part = Partition();
+  part.band = &B;
+  part.n_sub = n_sub;
+  part.n_overlap = n_overlap;
+  part.labels.assign(labels, labels + na);
+  return finish_partition(B, part);
+}
+
+// Everything after the split (Sec. 4.1 overlap and boundary sets, Sec. 4.2 Lambda_j and
+// CP_{S_j} generators, Sec. 5.2.2 cross points): a function of the labels, n_sub and N_O.
+static cpm_status finish_partition(const Band& B, Partition& part) {
+  const int n_sub = part.n_sub, n_overlap = part.n_overlap;
+  const int64_t na = B.n_active, N = B.n_nodes();
   std::vector<int64_t> count(n_sub, 0);
   for (int64_t g = 0; g < na; ++g) count[part.labels[g]]++;
   for (int l = 0; l < n_sub; ++l)

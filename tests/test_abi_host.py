@@ -221,3 +221,75 @@ def test_local_order_and_tile_envelope(case):
             blk = lu[64 * I:64 * I + 64]
             assert not np.any(blk[:, :64 * lo]), (j, I, lo)
             assert not np.any(blk[:, 64 * (hi + 1):]), (j, I, hi)
+
+
+def _slab_labels(cp, n_sub):
+    """Slabs along z by rank (a labelling the bisection would not produce)."""
+    order = np.lexsort((np.arange(len(cp)), cp[:, 2]))
+    lab = np.empty(len(cp), np.int32)
+    lab[order] = (np.arange(len(cp)) * n_sub) // len(cp)
+    return lab
+
+
+def test_partition_from_labels_matches_oracle_sets():
+    """Caller-supplied labels: every set equals the oracle's construction from the same labels
+    (Sec. 4.1 overlap and boundary sets, Sec. 4.2 generators, Sec. 5.2.2 cross marks)."""
+    h, no, ns = 0.1, 2, 5
+    band = G.cpm_build_band("sphere", 1.0, 0.0, h, 3)
+    OB = ob.build_band(geometry.make_surface("sphere", 1.0, 0.0), h, 3)
+    E = interp.extension_matrix(OB)
+    lab = _slab_labels(OB.cp[:OB.n_active], ns)
+    part = G.cpm_partition_from_labels(band, lab, no, ns)
+    assert np.array_equal(part.labels(), lab)
+    cross = partition.cross_point_nodes(OB, lab)
+    assert np.array_equal(part.cross_points(), cross)
+    marks = partition.CrossMarks(OB, cross, no)
+    for j in range(ns):
+        sub = partition.build_subdomain(OB, E, lab, j, no, robin=True)
+        for which, ref in [(G.CPM_SET_OWN, sub.own), (G.CPM_SET_SIGMA, sub.sigma),
+                           (G.CPM_SET_LAST, sub.last), (G.CPM_SET_GHOST, sub.ghost),
+                           (G.CPM_SET_BC_A, sub.bc_a), (G.CPM_SET_BC_G, sub.bc_g)]:
+            assert np.array_equal(part.set(j, which), ref), (j, which)
+        nodes = np.concatenate([sub.bc_a, sub.bc_g])
+        _, gen = partition.effective_boundary_cp(OB, sub, nodes)
+        assert np.array_equal(part.set(j, G.CPM_SET_BC_GEN), gen)
+        assert np.array_equal(part.set(j, G.CPM_SET_BC_NEARX).astype(bool), marks(nodes))
+    bad = lab.copy()
+    bad[0] = ns
+    with pytest.raises(G.CpmError) as e:
+        G.cpm_partition_from_labels(band, bad, no, ns)
+    assert e.value.status == _capi.CPM_ERR_INVALID_ARG
+    with pytest.raises(G.CpmError):                 # subdomain ns is empty
+        G.cpm_partition_from_labels(band, lab, no, ns + 1)
+
+
+def test_partition_checkpoint_round_trip(tmp_path):
+    band = G.cpm_build_band("torus", 1.0, 0.4, 0.05, 3)
+    part = G.cpm_partition(band, 6, [3, 1, 2, 5, 4, 1], 2, align_passes=2)
+    path = str(tmp_path / "part.bin")
+    G.cpm_partition_save(part, path)
+    back = G.cpm_partition_load(band, path)
+    assert back.n_sub == 6
+    assert np.array_equal(back.labels(), part.labels())
+    assert np.array_equal(back.cross_points(), part.cross_points())
+    for j in range(6):
+        for which in range(8):
+            assert np.array_equal(back.set(j, which), part.set(j, which)), (j, which)
+    # the same local operators come out of the reloaded partition
+    a = G.cpm_local_coo(band, part, 3.0, "oras", 4.0, 40.0, 2)
+    b = G.cpm_local_coo(band, back, 3.0, "oras", 4.0, 40.0, 2)
+    assert a[0] == b[0] and all(np.array_equal(x, y) for x, y in zip(a[1:], b[1:]))
+    # another band, a foreign file, a truncated file and a missing file are refused
+    other = G.cpm_build_band("torus", 1.0, 0.4, 0.1 / 2.0 + 1e-3, 3)
+    for bnd, p in [(other, path)]:
+        with pytest.raises(G.CpmError) as e:
+            G.cpm_partition_load(bnd, p)
+        assert e.value.status == _capi.CPM_ERR_INVALID_ARG
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a partition file at all" * 4)
+    trunc = tmp_path / "trunc.bin"
+    trunc.write_bytes(open(path, "rb").read()[:100])
+    for p in [str(junk), str(trunc), str(tmp_path / "missing.bin")]:
+        with pytest.raises(G.CpmError) as e:
+            G.cpm_partition_load(band, p)
+        assert e.value.status == _capi.CPM_ERR_INVALID_ARG
