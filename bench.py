@@ -537,6 +537,27 @@ def run_subdomain_table(args):
     print(json.dumps(out), flush=True)
 
 
+def run_peaks(args):
+    """FP64 FMA peak and dependent-FMA latency of this GPU (the FP64-ALU roofline denominator):
+    a sweep of block counts, block sizes and independent chains per thread."""
+    import torch
+    import paper_1909_08734_gb300 as G
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    rows = []
+    for threads in (128, 256, 512, 1024):
+        for per_sm in (1, 2, 4, 8):
+            if threads * per_sm > 2048:
+                continue
+            for chains in (1, 2, 4, 8):
+                tf, _ = G.cpm_probe_fp64(sms * per_sm, threads, chains, 4096, latency=False)
+                rows.append({"threads": threads, "blocks_per_sm": per_sm, "chains": chains,
+                             "tflop_s": round(tf, 4)})
+    _, lat = G.cpm_probe_fp64(1, 1, 1, 1 << 16, latency=True)
+    best = max(rows, key=lambda r: r["tflop_s"])
+    print(json.dumps({"fp64_fma_peak_tflop_s": best["tflop_s"], "best": best,
+                      "dependent_fma_cycles": round(lat, 2), "sms": sms, "sweep": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,6 +575,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-load", default="0.7", help="offered load(s), fractions of capacity")
     ap.add_argument("--serving-precisions", default="fp32,fp64")
+    ap.add_argument("--peaks", action="store_true",
+                    help="FP64 FMA peak / latency probe sweep (the FP64 roofline denominator)")
     ap.add_argument("--subdomain-table", action="store_true",
                     help="iteration counts against the paper's subdomain-count table")
     ap.add_argument("--table-subdomains", default="32,64,96")
@@ -562,7 +585,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
-    if args.kernel_only:
+    if args.peaks:
+        run_peaks(args)
+    elif args.kernel_only:
         run_kernel_only(args)
     elif args.serving:
         run_serving(args)

@@ -363,6 +363,17 @@ cpm_status cpm_vec_axpby(int64_t n, double a, const double* x_dev, double b, dou
  * completed, INVALID_ARG or CUDA otherwise. */
 cpm_status cpm_selftest_bounded_wait(oras_precond* pc, double limit_s, void* stream);
 
+/* FP64 fused multiply-add probe on the current device (the denominator of the FP64-ALU
+ * roofline fractions this library reports); no counterpart in the paper.  Throughput: `blocks`
+ * blocks of `threads` threads, each thread advancing `chains` (1, 2, 4 or 8) independent
+ * chains x <- x a + b for `iters` steps; *tflop_s = 2 threads blocks chains iters / (kernel
+ * time), timed with CUDA events after one warm-up launch.  Latency: one thread advancing one
+ * chain for `iters` steps; *cycles_per_fma = clock64 cycles per dependent step.  Either
+ * output pointer may be NULL to skip that probe.  Allocates and frees 64 KB of device memory;
+ * synchronises.  Errors: INVALID_ARG (blocks, threads or iters < 1, threads > 1024, chains not
+ * in {1, 2, 4, 8}), CUDA. */
+cpm_status cpm_probe_fp64(int blocks, int threads, int chains, int iters, double* tflop_s, double* cycles_per_fma);
+
 void oras_destroy(oras_precond* pc);
 
 const char* cpm_status_string(cpm_status s);

@@ -373,6 +373,15 @@ def cpm_vec_axpby(a: float, x, b: float, y, n: int | None = None, stream=None):
                                       _stream_ptr(stream)), "cpm_vec_axpby")
 
 
+def cpm_probe_fp64(blocks: int, threads: int, chains: int, iters: int = 4096, latency: bool = True):
+    """FP64 FMA probe: (TFLOP/s of the throughput kernel, cycles per dependent FMA or None)."""
+    t = C.c_double(0.0)
+    c = C.c_double(0.0)
+    _check(_capi.load().cpm_probe_fp64(int(blocks), int(threads), int(chains), int(iters), C.byref(t),
+                                       C.byref(c) if latency else None), "cpm_probe_fp64")
+    return t.value, (c.value if latency else None)
+
+
 def cpm_selftest_bounded_wait(pc: Preconditioner, limit_s: float = 0.2, stream=None) -> int:
     """Let a bounded device wait expire on purpose; returns the status (CPM_ERR_TIMEOUT)."""
     return int(_capi.load().cpm_selftest_bounded_wait(pc.handle, float(limit_s), _stream_ptr(stream)))

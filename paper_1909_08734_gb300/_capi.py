@@ -107,6 +107,8 @@ _SIGS = {
                                         C.POINTER(cpm_gmres_result), _P]),
     "cpm_vec_axpby": (C.c_int, [C.c_int64, C.c_double, _P, C.c_double, _P, _P]),
     "cpm_selftest_bounded_wait": (C.c_int, [_P, C.c_double, _P]),
+    "cpm_probe_fp64": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
     "oras_destroy": (None, [_P]),
     "cpm_status_string": (C.c_char_p, [C.c_int]),
     "cpm_last_error": (C.c_char_p, []),

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 HOST_SRC = ["host/band.cpp", "host/partition.cpp", "host/local_coo.cpp", "host/ordering.cpp", "capi_host.cpp"]
 CUDA_SRC = ["cuda/apply.cu", "cuda/factor.cu", "cuda/lu_tc.cu", "cuda/trsv.cu", "cuda/krylov.cu",
-            "cuda/stationary.cu", "cuda/selftest.cu", "capi_device.cu", "noalloc.cu"]
+            "cuda/stationary.cu", "cuda/selftest.cu", "cuda/probe.cu", "capi_device.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

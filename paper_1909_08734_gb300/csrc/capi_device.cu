@@ -50,8 +50,9 @@ void cpm::band_release_device(cpm::Band& b) {
   cudaFree(b.d_pencil);
   cudaFree(b.d_wts);
   cudaFree(b.d_nbr);
+  cudaFree(b.d_wt2);
   cudaSetDevice(cur);
-  b.d_pencil = b.d_wts = b.d_nbr = nullptr;
+  b.d_pencil = b.d_wts = b.d_nbr = b.d_wt2 = nullptr;
   b.d_device = -1;
 }
 
@@ -82,15 +83,22 @@ struct oras_precond {
   OperatorDev op{};
   double* v_scratch = nullptr;     // extension values for cpm_op_apply (nrhs x N)
   int64_t v_scratch_rhs = 0;
-  double* g_vext = nullptr;        // extension values owned by the FGMRES path
+  double* g_vext = nullptr;        // extension values owned by the FGMRES path (g_vext_rhs x N)
+  int g_vext_rhs = 0;
   // FGMRES workspace
   int g_m = 0;
   GmresDev gm{};
-  double* g_state_host = nullptr;
-  int* g_istate_host = nullptr;
+  double* g_state_host = nullptr;  // pinned: TRSV_MAX_NR x 8 scalars
+  int* g_istate_host = nullptr;    // pinned: TRSV_MAX_NR x GMRES_IST_STRIDE state ints, then 4 control ints
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t iter_graph = nullptr;
-  int graph_m = 0;
+  cudaGraphExec_t iter_graph[4] = {nullptr, nullptr, nullptr, nullptr};   // one per batch width 1, 2, 4, 8
+  void drop_graphs() {
+    for (auto& gx : iter_graph)
+      if (gx) {
+        cudaGraphExecDestroy(gx);
+        gx = nullptr;
+      }
+  }
   // stationary solver workspace
   double *st_z = nullptr, *st_r = nullptr, *st_part = nullptr, *st_norm = nullptr;
   double* st_norm_host = nullptr;
@@ -119,7 +127,7 @@ struct oras_precond {
     int cur = -1;
     cudaGetDevice(&cur);
     if (device >= 0) cudaSetDevice(device);
-    if (iter_graph) cudaGraphExecDestroy(iter_graph);
+    drop_graphs();
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto& b : bufs) cudaFree(b.p);
     if (g_state_host) cudaFreeHost(g_state_host);
@@ -144,6 +152,11 @@ cpm_status ensure_band_on_device(const cpm::Band& B, int dev) {
   CK(upload(B.pencil, &B.d_pencil));
   CK(upload(B.wts, &B.d_wts));
   CK(upload(B.nbr, &B.d_nbr));
+  const int P = B.P();
+  const int64_t nn = B.n_nodes();
+  CK(cudaMalloc(&B.d_wt2, sizeof(double) * (size_t)(P * P + P) * nn));
+  CK(launch_build_tensor_weights((const double*)B.d_wts, (double*)B.d_wt2, nn, P, 0));
+  CK(cudaDeviceSynchronize());
   B.d_device = dev;
   return CPM_OK;
 }
@@ -187,10 +200,7 @@ cpm_status set_schedule(oras_precond* pc, int ctas_per_sm, int kseg, int prefetc
   t.prefetch = prefetch;
   t.grid = sm_count(pc->device) * ctas_per_sm;
   pc->solve_ctas = ctas_per_sm;
-  if (pc->iter_graph) {
-    cudaGraphExecDestroy(pc->iter_graph);
-    pc->iter_graph = nullptr;
-  }
+  pc->drop_graphs();
   return CPM_OK;
 }
 
@@ -514,6 +524,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   op.P = B.P();
   op.diag = c + 6.0 / (B.h * B.h);
   op.invh2 = 1.0 / (B.h * B.h);
+  op.wt2 = (const double*)B.d_wt2;
   return CPM_OK;
 }
 
@@ -527,104 +538,151 @@ cpm_status ensure_v_scratch(oras_precond* pc, int nrhs) {
   return CPM_OK;
 }
 
-cpm_status ensure_gmres(oras_precond* pc, int m) {
-  if (pc->g_m == m) return CPM_OK;
+int width_index(int nr) { return nr >= 8 ? 3 : (nr >= 4 ? 2 : (nr >= 2 ? 1 : 0)); }
+
+// FGMRES workspace for restart length m and batches of up to nr right-hand sides (1, or
+// TRSV_MAX_NR once a batch is asked for).  Rows are split into blocks of a multiple of 32
+// rows, one block per SM (more for very long vectors, so that a block's rows fit in shared
+// memory); vectors have a leading dimension rounded up to 32 doubles.
+cpm_status ensure_gmres(oras_precond* pc, int m, int nr) {
+  const int cap = nr > 1 ? TRSV_MAX_NR : 1;
   GmresDev& g = pc->gm;
-  for (void* p : {(void*)g.V, (void*)g.Z, (void*)g.w, (void*)g.r, (void*)g.part, (void*)g.st, (void*)g.ist})
+  if (pc->g_m == m && g.nrhs >= cap) return CPM_OK;
+  for (void* p : {(void*)g.V, (void*)g.Z, (void*)g.w, (void*)g.r, (void*)g.part, (void*)g.st, (void*)g.ist,
+                  (void*)g.ctl})
     if (p) pc->release(p);
-  if (pc->iter_graph) {
-    cudaGraphExecDestroy(pc->iter_graph);
-    pc->iter_graph = nullptr;
-  }
+  pc->drop_graphs();
   g = GmresDev{};
   pc->g_m = 0;
   const int64_t n = pc->n_active;
   g.n = n;
+  g.ld = (n + 31) / 32 * 32;
   g.m = m;
-  // one block of 256 threads per SM for the Arnoldi kernels (rows split evenly)
-  g.nblk = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count(pc->device));
-  if (g.nblk < 1) g.nblk = 1;
-  ALLOC(g.V, double, (int64_t)(m + 1) * n);
-  ALLOC(g.Z, double, (int64_t)m * n);
-  ALLOC(g.w, double, n);
-  ALLOC(g.r, double, n);
-  ALLOC(g.part, double, (int64_t)g.nblk * (m + 2));
-  ALLOC(g.st, double, gmres_state_size(m));
-  ALLOC(g.ist, int, 16);
-  CK(cudaMemset(g.ist, 0, 16 * sizeof(int)));
-  if (!pc->g_istate_host) CK(cudaMallocHost(&pc->g_istate_host, 8 * sizeof(int)));
-  if (!pc->g_state_host) CK(cudaMallocHost(&pc->g_state_host, 8 * sizeof(double)));
+  g.nrhs = cap;
+  g.status = pc->status;
+  const int64_t sms = sm_count(pc->device);
+  int64_t nblk = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sms));
+  int64_t chunk = ((n + nblk - 1) / nblk + 31) / 32 * 32;
+  const int64_t MAX_CHUNK = gmres_max_chunk();   // rows per block (shared memory)
+  if (chunk > MAX_CHUNK) chunk = MAX_CHUNK;
+  nblk = (n + chunk - 1) / chunk;
+  g.nblk = (int)std::max<int64_t>(1, nblk);
+  g.chunk = (int)chunk;
+  g.st_stride = (gmres_state_size(m) + 7) / 8 * 8;
+  g.part_stride = (int64_t)g.nblk * (2 * (m + 1) + 1);
+  ALLOC(g.V, double, (int64_t)cap * (m + 1) * g.ld);
+  ALLOC(g.Z, double, (int64_t)cap * (m + 1) * g.ld);
+  ALLOC(g.w, double, (int64_t)cap * g.ld);
+  ALLOC(g.r, double, (int64_t)cap * g.ld);
+  ALLOC(g.part, double, (int64_t)cap * g.part_stride);
+  ALLOC(g.st, double, (int64_t)cap * g.st_stride);
+  ALLOC(g.ist, int, cap * GMRES_IST_STRIDE);
+  ALLOC(g.ctl, int, 4);
+  CK(cudaMemset(g.V, 0, sizeof(double) * (size_t)cap * (m + 1) * g.ld));
+  CK(cudaMemset(g.Z, 0, sizeof(double) * (size_t)cap * (m + 1) * g.ld));
+  CK(cudaMemset(g.st, 0, sizeof(double) * (size_t)cap * g.st_stride));
+  CK(cudaMemset(g.ist, 0, sizeof(int) * cap * GMRES_IST_STRIDE));
+  CK(cudaMemset(g.ctl, 0, 4 * sizeof(int)));
+  CK(gmres_prepare(g.chunk, m));
+  if (!pc->g_istate_host)
+    CK(cudaMallocHost(&pc->g_istate_host, (TRSV_MAX_NR * GMRES_IST_STRIDE + 4) * sizeof(int)));
+  if (!pc->g_state_host) CK(cudaMallocHost(&pc->g_state_host, TRSV_MAX_NR * 8 * sizeof(double)));
+  if (pc->g_vext_rhs < cap) {
+    if (pc->g_vext) pc->release(pc->g_vext);
+    pc->g_vext = nullptr;
+    pc->g_vext_rhs = 0;
+    ALLOC(pc->g_vext, double, (int64_t)cap * pc->n_nodes);
+    pc->g_vext_rhs = cap;
+  }
   pc->g_m = m;
-  if (!pc->g_vext) ALLOC(pc->g_vext, double, pc->n_nodes);
   return CPM_OK;
 }
 
-// One FGMRES iteration: z_k = M^{-1} v_k, w = A z_k, CGS2, Givens.
-cpm_status launch_iteration(oras_precond* pc, cudaStream_t s) {
+// One FGMRES iteration of nr right-hand sides: z_k = M^{-1} v_k (one solve launch for all of
+// them), vext = E z_k, then w = A z_k, CGS2 and Givens.  A right-hand side whose cycle has
+// stopped points its solve at the spare slot m and skips the Arnoldi kernels; once none runs,
+// every kernel returns at once.
+cpm_status launch_iteration(oras_precond* pc, int nr, cudaStream_t s) {
   GmresDev& g = pc->gm;
-  const int* done = g.ist + 2;
-  IndirectVec vk{g.V, 0, g.ist, g.n, 0};
-  IndirectVec zk{g.Z, 0, g.ist, g.n, 0};
-  CK(launch_trsv(pc->trsv, vk, zk, done, s));
-  CK(launch_ext_values(pc->op, zk, pc->g_vext, 1, done, s));
-  CK(launch_cgs2_and_givens(g, pc->op, zk, pc->g_vext, s));
+  const int* alldone = g.ctl + 1;
+  const int64_t rs = (int64_t)(g.m + 1) * g.ld;
+  IndirectVec vk{g.V, rs, g.ist + GMRES_SLOT_INT, g.ld, 0, GMRES_IST_STRIDE,
+                 g.st + gmres_scalar_offset(g.m) + GMRES_VSCALE_DBL, g.st_stride};
+  IndirectVec zk{g.Z, rs, g.ist + GMRES_SLOT_INT, g.ld, 0, GMRES_IST_STRIDE};
+  CK(launch_trsv(pc->trsv, vk, zk, alldone, s, nr));
+  CK(launch_ext_values(pc->op, zk, pc->g_vext, nr, alldone, s));
+  CK(launch_arnoldi_step(g, pc->op, pc->g_vext, nr, s));
   pc->launches += KERNELS_PER_ITERATION;
   return CPM_OK;
 }
 
-cpm_status solve_one(oras_precond* pc, const double* f, double* u, const cpm_gmres_opts& o,
-                     cpm_gmres_result* res, cudaStream_t s) {
-  GmresDev& g = pc->gm;
-  if (o.zero_guess) CK(cudaMemsetAsync(u, 0, sizeof(double) * g.n, s));
-  CK(launch_gmres_begin(g, f, o.tol, o.max_it, s));
-  CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(g.r, 0), 1, 1, nullptr, s));
-  CK(launch_gmres_residual_check(g, s));
-  pc->launches += KERNELS_BEGIN + KERNELS_APPLY + KERNELS_RESIDUAL_CHECK;
-  for (;;) {
-    CK(cudaMemcpyAsync(pc->g_istate_host, g.ist, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (pc->g_istate_host[3] != -1) break;     // converged or failed
-    for (int it = 0; it < g.m; ++it) {
-      if (pc->iter_graph) {
-        CK(cudaGraphLaunch(pc->iter_graph, s));
-        pc->launches += KERNELS_PER_ITERATION;
-      }
-      else {
-        cpm_status st = launch_iteration(pc, s);
-        if (st != CPM_OK) return st;
-      }
-    }
-    CK(launch_gmres_restart_update(g, u, s));
-    CK(launch_apply(pc->op, direct(u, 0), pc->g_vext, f, direct(g.r, 0), 1, 1, nullptr, s));
-    CK(launch_gmres_residual_check(g, s));
-    pc->launches += KERNELS_RESTART_UPDATE + KERNELS_APPLY + KERNELS_RESIDUAL_CHECK;
-  }
-  CK(cudaMemcpy(pc->g_state_host, g.st + gmres_scalar_offset(g.m), 8 * sizeof(double),
-                cudaMemcpyDeviceToHost));
-  int dst = 0;
-  CK(cudaMemcpy(&dst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
-  res->iterations = pc->g_istate_host[1];
-  res->relres = pc->g_state_host[4];
-  res->status = pc->g_istate_host[3];
-  if (dst & ST_TIMEOUT) {
-    CK(cudaMemset(pc->status, 0, sizeof(int)));
-    res->status = CPM_ERR_TIMEOUT;
-  }
-  return CPM_OK;
-}
-
-cpm_status capture_graph(oras_precond* pc) {
+cpm_status capture_graph(oras_precond* pc, int nr) {
   if (!pc->cap_stream) CK(cudaStreamCreateWithFlags(&pc->cap_stream, cudaStreamNonBlocking));
   cudaGraph_t graph;
   CK(cudaStreamBeginCapture(pc->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cpm_status st = launch_iteration(pc, pc->cap_stream);
+  const int64_t before = pc->launches;
+  cpm_status st = launch_iteration(pc, nr, pc->cap_stream);
+  pc->launches = before;
   cudaError_t e = cudaStreamEndCapture(pc->cap_stream, &graph);
   if (st != CPM_OK) return st;
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&pc->iter_graph, graph, 0);
+  e = cudaGraphInstantiate(&pc->iter_graph[width_index(nr)], graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-  pc->graph_m = pc->g_m;
+  return CPM_OK;
+}
+
+// nr (1, 2, 4 or 8) right-hand sides solved in lock step.  Every right-hand side runs the
+// operations of a single-rhs solve; the batch shares launches and the factor stream.
+cpm_status solve_batch(oras_precond* pc, const double* f, double* u, int nr, const cpm_gmres_opts& o,
+                       bool use_graph, cpm_gmres_result* res, cudaStream_t s) {
+  GmresDev& g = pc->gm;
+  const int64_t n = pc->n_active;
+  int* ih = pc->g_istate_host;
+  int* ctl_h = ih + TRSV_MAX_NR * GMRES_IST_STRIDE;
+  if (o.zero_guess) CK(cudaMemsetAsync(u, 0, sizeof(double) * n * nr, s));
+  CK(launch_gmres_begin(g, f, n, o.tol, o.max_it, nr, s));
+  CK(launch_apply(pc->op, direct(u, n), pc->g_vext, f, direct(g.r, g.ld), nr, 1, nullptr, s));
+  CK(launch_gmres_residual_check(g, nr, s));
+  pc->launches += KERNELS_BEGIN + KERNELS_APPLY + KERNELS_RESIDUAL_CHECK;
+  cudaGraphExec_t gx = use_graph ? pc->iter_graph[width_index(nr)] : nullptr;
+  for (;;) {
+    CK(cudaMemcpyAsync(ih, g.ist, sizeof(int) * nr * GMRES_IST_STRIDE, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int live = 0;
+    for (int q = 0; q < nr; ++q) live += ih[q * GMRES_IST_STRIDE + 3] == -1;   // status RUNNING
+    if (live == 0) break;
+    ctl_h[0] = live;
+    ctl_h[1] = 0;
+    CK(cudaMemcpyAsync(g.ctl, ctl_h, 2 * sizeof(int), cudaMemcpyHostToDevice, s));
+    for (int it = 0; it < g.m; ++it) {
+      if (gx) {
+        CK(cudaGraphLaunch(gx, s));
+        pc->launches += KERNELS_PER_ITERATION;
+      } else {
+        cpm_status st = launch_iteration(pc, nr, s);
+        if (st != CPM_OK) return st;
+      }
+    }
+    CK(launch_gmres_restart_update(g, u, n, nr, s));
+    CK(launch_apply(pc->op, direct(u, n), pc->g_vext, f, direct(g.r, g.ld), nr, 1, nullptr, s));
+    CK(launch_gmres_residual_check(g, nr, s));
+    pc->launches += KERNELS_RESTART_UPDATE + KERNELS_APPLY + KERNELS_RESIDUAL_CHECK;
+  }
+  CK(cudaMemcpy2DAsync(pc->g_state_host, 8 * sizeof(double), g.st + gmres_scalar_offset(g.m),
+                       sizeof(double) * g.st_stride, 8 * sizeof(double), nr, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int dst = 0;
+  CK(cudaMemcpy(&dst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
+  for (int q = 0; q < nr; ++q) {
+    res[q].iterations = ih[q * GMRES_IST_STRIDE + 1];
+    res[q].relres = pc->g_state_host[q * 8 + 4];
+    res[q].status = ih[q * GMRES_IST_STRIDE + 3];
+  }
+  if (dst & ST_TIMEOUT) {
+    CK(cudaMemset(pc->status, 0, sizeof(int)));
+    for (int q = 0; q < nr; ++q) res[q].status = CPM_ERR_TIMEOUT;
+  }
   return CPM_OK;
 }
 
@@ -637,7 +695,10 @@ cpm_status ensure_stationary(oras_precond* pc) {
   ALLOC(pc->st_part, double, pc->st_nblk);
   ALLOC(pc->st_norm, double, TRSV_MAX_NR);
   if (!pc->st_norm_host) CK(cudaMallocHost(&pc->st_norm_host, TRSV_MAX_NR * sizeof(double)));
-  if (!pc->g_vext) ALLOC(pc->g_vext, double, pc->n_nodes);
+  if (!pc->g_vext) {
+    ALLOC(pc->g_vext, double, pc->n_nodes);
+    pc->g_vext_rhs = 1;
+  }
   return CPM_OK;
 }
 
@@ -727,10 +788,7 @@ cpm_status ensure_multi_rhs(oras_precond* pc) {
   t.ytag = y;
   t.ptag = pt;
   t.nr_cap = TRSV_MAX_NR;
-  if (pc->iter_graph) {
-    cudaGraphExecDestroy(pc->iter_graph);
-    pc->iter_graph = nullptr;
-  }
+  pc->drop_graphs();
   return CPM_OK;
 }
 
@@ -839,7 +897,8 @@ cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmissio
   // every allocation may be rounded up to a 2 MiB page
   const int64_t page = 2 << 20;
   auto rnd = [&](int64_t b) { return ((b + page - 1) / page) * page; };
-  const int64_t band_dev = rnd(4 * NN * B.P() * B.P()) + rnd(8 * NN * 3 * B.P()) + rnd(4 * N * 6);
+  const int64_t band_dev = rnd(4 * NN * B.P() * B.P()) + rnd(8 * NN * 3 * B.P()) + rnd(4 * N * 6) +
+                         rnd(8 * NN * (B.P() * B.P() + B.P())) /* tensor weights */;
   const int64_t work = rnd(wb * tile_elems);
   const int64_t inv = rnd(2 * wb * rows * TILE);
   const int64_t small = rnd(sizeof(SubMeta) * ns) + 2 * rnd(4 * rows) + rnd(4) + rnd(16);
@@ -854,10 +913,14 @@ cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmissio
   const int64_t nrc = nrhs > 1 ? TRSV_MAX_NR : 1;       // tagged words per row and rhs slot
   const int64_t sched = rnd(8 * (int64_t)items.size()) + rnd(8 * words * (rows / TILE) * maxseg * TILE * nrc) +
                         rnd(8 * words * rows * nrc) + rnd(16);
-  const int64_t nblk = 152;
-  const int64_t gmres = rnd(8 * (restart + 1) * N) + rnd(8 * restart * N) + 2 * rnd(8 * N) +
-                        rnd(8 * nblk * (restart + 2)) + rnd(8 * (int64_t)(restart + 2) * (restart + 8) + 4096) +
-                        rnd(64) + rnd(8 * NN) /* extension values */ + rnd(8 * nrhs * NN) /* apply scratch */;
+  // FGMRES workspace of the lock-step batch (1 right-hand side, or TRSV_MAX_NR for batches)
+  const int64_t cap = nrhs > 1 ? TRSV_MAX_NR : 1;
+  const int64_t ld = (N + 31) / 32 * 32;
+  const int64_t nblk = std::max<int64_t>(152, (N + 16383) / 16384);
+  const int64_t gmres = 2 * rnd(8 * cap * (restart + 1) * ld) + 2 * rnd(8 * cap * ld) +
+                        rnd(8 * cap * nblk * (2 * (restart + 1) + 1)) +
+                        rnd(8 * cap * ((int64_t)(restart + 2) * (restart + 8) + 64)) + rnd(4 * cap * 16) + rnd(16) +
+                        rnd(8 * cap * NN) /* extension values */ + rnd(8 * nrhs * NN) /* apply scratch */;
   const int64_t ubuf = precision == CPM_FP64 ? 0 : rnd((int64_t)lu_tc_ubuf_bytes(rows / TILE, precision == CPM_BF16));
   const int64_t envelope = 2 * rnd(4 * rows) + rnd(4 * (int64_t)ns * t_max) + rnd(4 * ns);
   const int64_t setup_peak = band_dev + work + inv + small + assembly + ubuf + envelope +
@@ -1011,26 +1074,27 @@ cpm_status cpm_gmres_solve(const oras_precond* cpc, const double* f_dev, double*
     return CPM_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  cpm_status st = ensure_gmres(pc, o.restart);
+  const int64_t n = pc->n_active;
+  const int widest = nr_chunk(nrhs);
+  cpm_status st = ensure_gmres(pc, o.restart, widest);
   if (st != CPM_OK) return st;
-  if (o.use_graph && !pc->iter_graph) {
-    st = capture_graph(pc);
+  if (widest > 1) {
+    st = ensure_multi_rhs(pc);
     if (st != CPM_OK) return st;
   }
-  const bool had_graph = pc->iter_graph != nullptr;
-  cudaGraphExec_t saved = pc->iter_graph;
-  if (!o.use_graph) pc->iter_graph = nullptr;
   cpm_status first = CPM_OK;
-  for (int i = 0; i < nrhs; ++i) {
-    st = solve_one(pc, f_dev + (int64_t)i * pc->n_active, u_dev + (int64_t)i * pc->n_active, o,
-                   &results[i], s);
-    if (st != CPM_OK) {
-      if (had_graph) pc->iter_graph = saved;
-      return st;
+  for (int i = 0; i < nrhs;) {
+    const int nr = nr_chunk(nrhs - i);
+    if (o.use_graph && !pc->iter_graph[width_index(nr)]) {
+      st = capture_graph(pc, nr);
+      if (st != CPM_OK) return st;
     }
-    if (first == CPM_OK && results[i].status != CPM_OK) first = (cpm_status)results[i].status;
+    st = solve_batch(pc, f_dev + (int64_t)i * n, u_dev + (int64_t)i * n, nr, o, o.use_graph != 0, &results[i], s);
+    if (st != CPM_OK) return st;
+    for (int q = 0; q < nr; ++q)
+      if (first == CPM_OK && results[i + q].status != CPM_OK) first = (cpm_status)results[i + q].status;
+    i += nr;
   }
-  if (had_graph) pc->iter_graph = saved;
   if (first != CPM_OK) cpm::set_error(std::string("cpm_gmres_solve: ") + cpm_status_string(first));
   return first;
 }
@@ -1102,6 +1166,42 @@ cpm_status cpm_selftest_bounded_wait(oras_precond* pc, double limit_s, void* str
     cpm::set_error("cpm_selftest_bounded_wait: both bounded waits expired (expected)");
     return CPM_ERR_TIMEOUT;
   }
+  return CPM_OK;
+}
+
+cpm_status cpm_probe_fp64(int blocks, int threads, int chains, int iters, double* tflop_s, double* cycles_per_fma) {
+  if (blocks < 1 || threads < 1 || threads > 1024 || iters < 1 ||
+      (chains != 1 && chains != 2 && chains != 4 && chains != 8)) {
+    cpm::set_error("cpm_probe_fp64: need blocks, iters >= 1, 1 <= threads <= 1024, chains in {1, 2, 4, 8}");
+    return CPM_ERR_INVALID_ARG;
+  }
+  double* buf = nullptr;
+  CK(cudaMalloc(&buf, 65536));
+  long long* cyc = (long long*)(buf + 4096);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int nb = std::min(blocks, 4096);
+  if (e == cudaSuccess && tflop_s) {
+    e = launch_fma_throughput(nb, threads, chains, iters, buf, 0);          // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) e = launch_fma_throughput(nb, threads, chains, iters, buf, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) *tflop_s = 2.0 * nb * (double)threads * chains * iters / (ms * 1e-3) / 1e12;
+  }
+  if (e == cudaSuccess && cycles_per_fma) {
+    e = launch_fma_latency(iters, buf, cyc, 0);
+    long long c = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&c, cyc, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) *cycles_per_fma = (double)c / iters;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(e, "cpm_probe_fp64");
   return CPM_OK;
 }
 

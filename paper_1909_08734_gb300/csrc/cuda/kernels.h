@@ -10,17 +10,27 @@
 
 namespace cpmdev {
 
-// A vector whose address may depend on a device-resident index k (so that one captured
-// CUDA graph serves every Krylov step): ptr(r) = base + r*rhs_stride + (*k + k_add)*k_stride.
+// A vector whose address may depend on a device-resident index (so that one captured CUDA
+// graph serves every Krylov step): column r is
+//   base + r*rhs_stride + (k[r*k_rhs_stride] + k_add)*k_stride      (k null: base + r*rhs_stride)
+// and load() multiplies by scale[r*scale_rhs_stride] when scale is set (a basis vector stored
+// unnormalised together with its scale).
 struct IndirectVec {
   double* base;
   int64_t rhs_stride;
   const int* k;
   int64_t k_stride;
   int k_add;
+  int k_rhs_stride = 0;
+  const double* scale = nullptr;
+  int scale_rhs_stride = 0;
   __device__ __forceinline__ double* ptr(int r) const {
-    int kk = k ? (*k + k_add) : 0;
+    int kk = k ? (k[r * k_rhs_stride] + k_add) : 0;
     return base + (int64_t)r * rhs_stride + (int64_t)kk * k_stride;
+  }
+  __device__ __forceinline__ double load(int r, int64_t i) const {
+    const double v = ptr(r)[i];
+    return scale ? v * scale[r * scale_rhs_stride] : v;
   }
 };
 inline IndirectVec direct(double* p, int64_t rhs_stride) { return IndirectVec{p, rhs_stride, nullptr, 0, 0}; }
@@ -32,13 +42,18 @@ struct OperatorDev {
   int64_t n_active, n_nodes;
   int P;
   double diag, invh2;
+  const double* wt2 = nullptr;   // (P^2 + P) x N tensor weights (build_tensor_weights), or null
 };
+// wt2[(b P + c) N + k] = wy_b(k) wz_c(k) and wt2[(P^2 + a) N + k] = wx_a(k) for every band node
+// k, from the 1-D weights (N x 3 x P); the extension kernel then needs P^3 + P multiply-adds
+// per node instead of P^3 + P^2 + P plus a lane reduction.
+cudaError_t launch_build_tensor_weights(const double* wts, double* wt2, int64_t n_nodes, int P, cudaStream_t s);
 
 // kernels issued by each launcher (for the handle's launch counter)
 constexpr int KERNELS_APPLY = 2;
 constexpr int KERNELS_TRSV = 1;
 constexpr int KERNELS_EXT_VALUES = 1;
-constexpr int KERNELS_CGS2_GIVENS = 4;   // operator second half fused into the first of them
+constexpr int KERNELS_CGS2_GIVENS = 3;   // operator second half fused into the first of them
 constexpr int KERNELS_PER_ITERATION = KERNELS_TRSV + KERNELS_EXT_VALUES + KERNELS_CGS2_GIVENS;
 constexpr int KERNELS_BEGIN = 1;
 constexpr int KERNELS_RESTART_UPDATE = 2;
@@ -47,6 +62,10 @@ constexpr int KERNELS_RESIDUAL_CHECK = 2;
 // ---- expiry of the bounded waits (test entry point) ----
 cudaError_t launch_bounded_wait_selftest(uint64_t limit_ns, const uint32_t* never, int* status, int* out,
                                          cudaStream_t s);
+
+// ---- FP64 FMA probes ----
+cudaError_t launch_fma_throughput(int blocks, int threads, int chains, int iters, double* out, cudaStream_t s);
+cudaError_t launch_fma_latency(int iters, double* out, long long* cycles, cudaStream_t s);
 
 // ---- stationary (O)RAS solver vectors ----
 constexpr int KERNELS_AXPY = 1;
@@ -141,26 +160,43 @@ void trsv_build_items(const int* T, int n_sub, int kseg, int stagger, std::vecto
                       int* maxseg, const int32_t* tlo = nullptr, const int32_t* thi = nullptr);
 
 // ---- Krylov kernels ----
+// FGMRES(m) state of up to nrhs right-hand sides advanced in lock step (right-hand side q at
+// offset q times the per-rhs size of every array).
+constexpr int GMRES_IST_STRIDE = 16;   // state ints per right-hand side
+constexpr int GMRES_SLOT_INT = 6;      // state int: basis / direction slot the solve reads and writes
+constexpr int GMRES_VSCALE_DBL = 5;    // scalar: scale of the stored basis vector V[k]
 struct GmresDev {
-  double* V;        // (m+1) x N
-  double* Z;        // m x N
-  double* w;        // N
-  double* r;        // N
-  double* part;     // partial sums [nblk][m+2]
-  double* st;       // state doubles: H, cs, sn, g, y, scalars
-  int* ist;         // state ints: [0] k, [1] total, [2] done, [3] status, [4] kdone, [5] max_it
-  int64_t n;
+  double* V;        // nrhs x (m+1) x ld: basis; V[k+1] holds w unnormalised until step k+1 scales it
+  double* Z;        // nrhs x (m+1) x ld: preconditioned directions (slot m: the solves of a finished rhs)
+  double* w;        // nrhs x ld
+  double* r;        // nrhs x ld
+  double* part;     // nrhs x part_stride: block partial sums of h1, h2 and ||w||^2
+  double* st;       // nrhs x st_stride: H, cs, sn, g, y, h1, scalars
+  int* ist;         // nrhs x GMRES_IST_STRIDE: [0] k, [1] total, [2] done, [3] status, [4] kdone,
+                    // [5] max_it, [6] slot (k, or m once the cycle stopped), [8..11] tickets
+  int* ctl;         // [0] right-hand sides whose cycle runs, [1] 1 once none does
+  int* status;      // device status word (bounded waits that gave up: ST_TIMEOUT)
+  int64_t n;        // rows (N_A)
+  int64_t ld;       // leading dimension of the vectors (n rounded up)
   int m;
-  int nblk;
+  int nblk;         // blocks per right-hand side of the vector kernels
+  int chunk;        // rows per block
+  int nrhs;         // right-hand sides the arrays hold
+  int st_stride;
+  int64_t part_stride;
 };
 int gmres_state_size(int m);       // doubles of state for restart length m
-int gmres_scalar_offset(int m);     // offset of the scalars (||f||, tol, beta, ||w||, relres)
-cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, double tol, int max_it,
-                               cudaStream_t s);
-// After launch_ext_values(z_k) into vext: w = A z_k, CGS2, Givens, v_{k+1} (four kernels).
-cudaError_t launch_cgs2_and_givens(const GmresDev& g, const OperatorDev& op, IndirectVec z, const double* vext,
-                                   cudaStream_t s);
-cudaError_t launch_gmres_restart_update(const GmresDev& g, double* u, cudaStream_t s);
-cudaError_t launch_gmres_residual_check(const GmresDev& g, cudaStream_t s);
+int gmres_scalar_offset(int m);     // offset of the scalars (||f||, tol, beta, ||w||, relres, scale)
+size_t gmres_step_smem_bytes(int chunk);
+int gmres_max_chunk();             // most rows per block of the step kernels
+cudaError_t gmres_prepare(int chunk, int m);   // once per device and shape, before the launches
+// begin: ||f_q|| (f_q = f + q f_stride), tolerance, iteration limit, for nr right-hand sides
+cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, int64_t f_stride, double tol, int max_it,
+                               int nr, cudaStream_t s);
+// After launch_ext_values(z_k) into vext: w = A z_k, CGS2, Givens (three kernels).
+cudaError_t launch_arnoldi_step(const GmresDev& g, const OperatorDev& op, const double* vext, int nr,
+                                cudaStream_t s);
+cudaError_t launch_gmres_restart_update(const GmresDev& g, double* u, int64_t u_stride, int nr, cudaStream_t s);
+cudaError_t launch_gmres_residual_check(const GmresDev& g, int nr, cudaStream_t s);
 
 }  // namespace cpmdev

@@ -1,16 +1,30 @@
 // Device-resident right-preconditioned flexible GMRES(m) with CGS2 (Sec. 2.2: the (O)RAS
-// preconditioner inside GMRES).  All Arnoldi arithmetic is FP64.
+// preconditioner inside GMRES) for 1..8 right-hand sides advanced in lock step.  All Arnoldi
+// arithmetic is FP64.
 //
-// Reductions are deterministic: every block writes its partial sums, and the last block to
-// finish (ticket counter) adds the partials in block order.  The step index k, the
-// cycle-done flag and the status live in device memory, so one captured CUDA graph of an
-// iteration replays for every k; every kernel of an iteration returns at once when the
-// cycle is already done.  One Arnoldi step after z_k = M^{-1} v_k and w = A z_k is four
-// kernels:
-//   dots    : h1 = V_k^T w                                   (first Gram-Schmidt pass)
-//   update1 : w -= V_k h1 ;  h2 = V_k^T w                    (second pass)
-//   update2 : w -= V_k h2 ;  ||w||, Hessenberg column, Givens rotation, stopping test
-//   scale   : v_{k+1} = w / ||w|| ;  k += 1
+// FP64 instructions are the scarce resource here (this GPU issues two FP64 lanes per SM and
+// clock, 1/64 of its FP32 rate), so the kernels issue as few as the method needs:
+//  * dot products V_k^T w: a warp owns whole basis vectors (lanes read consecutive rows) and
+//    leaves 32 lane partials per vector, which one thread then adds; a shuffle tree per value
+//    and warp would cost 5 x 32 lane additions per value;
+//  * updates w -= V_k h: one thread per row and no reduction;
+//  * block partials are added by every block of the consuming kernel in one fixed order
+//    (deterministic, no atomics); only the norm's last block finishes the step;
+//  * v_{k+1} = w / ||w|| is no pass of its own: a step stores w unnormalised in V[k+1] with the
+//    scale 1/||w||; the next solve multiplies while it gathers (IndirectVec::scale) and the next
+//    step's first kernel normalises V[k+1] in place as it reads it.
+// The kernels of a step use programmatic dependent launch: a kernel may be scheduled while its
+// predecessor runs and waits (griddepcontrol.wait) before it reads anything.
+//
+// Right-hand side q is blockIdx.y; its state (step k, done flag, status, ...) lives in device
+// memory, so one captured CUDA graph of an iteration replays for every k, and every kernel of
+// an iteration returns at once for a right-hand side whose cycle has stopped.  Each right-hand
+// side follows exactly the operations of a single-rhs solve (the batch only shares launches and
+// the factor stream of the solves).  One Arnoldi step after z_k = M^{-1} v_k, vext = E z_k:
+//   wdots : w = A z_k (operator second half);  V[k] *= s;  partial h1 = V_k^T w
+//   upd1  : h1 = sum of partials;  w -= V_k h1;  partial h2 = V_k^T w
+//   upd2  : h2 = sum of partials;  w -= V_k h2 -> V[k+1];  partial ||w||^2;  last block:
+//           Hessenberg column, Givens rotation, stopping test, s = 1/||w||, k += 1
 #include <math.h>
 
 #include "../../../include/cpm.h"
@@ -19,14 +33,18 @@
 
 namespace cpmdev {
 
-constexpr int KT = 256;                 // threads per block of the vector kernels
+constexpr int KT = 256;                 // threads per block of the restart vector kernels
 constexpr int KW = KT / 32;
-constexpr int ILP = 8;                  // basis vectors processed together
+constexpr int ST = 512;                 // threads per block of the Arnoldi step kernels
+constexpr int SW = ST / 32;             // their warps (four per scheduler: latency hiding)
+constexpr int MAX_UNITS = 128;          // basis vectors of one step (m + 1 <= 128)
 
-// int state
-enum { I_K = 0, I_TOTAL = 1, I_DONE = 2, I_STATUS = 3, I_KDONE = 4, I_MAXIT = 5,
-       I_TICKET = 8 };                  // tickets 8..11, one per reducing kernel
+// int state per right-hand side (GMRES_IST_STRIDE ints)
+enum { I_K = 0, I_TOTAL = 1, I_DONE = 2, I_STATUS = 3, I_KDONE = 4, I_MAXIT = 5, I_SLOT = 6,
+       I_TICKET = 8 };                  // tickets 8..11
 constexpr int RUNNING = -1;
+// batch control words
+enum { C_LIVE = 0, C_ALLDONE = 1 };
 
 // double state layout for restart length m
 struct SL {
@@ -37,190 +55,428 @@ struct SL {
   __host__ __device__ int g() const { return sn() + m; }
   __host__ __device__ int y() const { return g() + m + 1; }
   __host__ __device__ int h1() const { return y() + m; }
-  __host__ __device__ int h2() const { return h1() + m + 1; }
-  __host__ __device__ int sc() const { return h2() + m + 1; }   // scalars
+  __host__ __device__ int sc() const { return h1() + m + 1; }   // scalars
 };
-enum { S_NF = 0, S_TOL = 1, S_BETA = 2, S_HN = 3, S_RELRES = 4 };
+enum { S_NF = 0, S_TOL = 1, S_BETA = 2, S_HN = 3, S_RELRES = 4, S_VSCALE = 5 };
+static_assert(I_SLOT == GMRES_SLOT_INT && S_VSCALE == GMRES_VSCALE_DBL, "state layout shared with the host");
 
-__device__ __forceinline__ bool cycle_done(const GmresDev& g) {
-  return *(volatile const int*)&g.ist[I_DONE] != 0;
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// views of right-hand side q
+struct Rhs {
+  double *V, *Z, *w, *r, *st, *p1, *p2, *p3;
+  int* ist;
+};
+__device__ __forceinline__ Rhs rhs_view(const GmresDev& g, int q) {
+  Rhs v;
+  v.V = g.V + (int64_t)q * (g.m + 1) * g.ld;
+  v.Z = g.Z + (int64_t)q * (g.m + 1) * g.ld;
+  v.w = g.w + (int64_t)q * g.ld;
+  v.r = g.r + (int64_t)q * g.ld;
+  v.st = g.st + (int64_t)q * g.st_stride;
+  v.p1 = g.part + (int64_t)q * g.part_stride;
+  v.p2 = v.p1 + (int64_t)g.nblk * (g.m + 1);
+  v.p3 = v.p2 + (int64_t)g.nblk * (g.m + 1);
+  v.ist = g.ist + q * GMRES_IST_STRIDE;
+  return v;
 }
 
-__device__ __forceinline__ void block_rows(const GmresDev& g, int64_t* r0, int64_t* r1) {
-  const int64_t chunk = (g.n + g.nblk - 1) / g.nblk;
-  *r0 = blockIdx.x * chunk;
-  *r1 = min(g.n, *r0 + chunk);
+__device__ __forceinline__ bool stopped(const Rhs& v) { return *(volatile const int*)&v.ist[I_DONE] != 0; }
+
+// this block's rows [r0, r0 + nr)
+__device__ __forceinline__ int block_rows(const GmresDev& g, int64_t* r0) {
+  *r0 = (int64_t)blockIdx.x * g.chunk;
+  const int64_t e = min(g.n, *r0 + (int64_t)g.chunk);
+  return (int)max((int64_t)0, e - *r0);
 }
 
-// Block partial sums s[i] (i < cnt, held in shared memory wp[KW][...]) -> part[b][i].
-// Then the last block adds all blocks' partials in a fixed order into out[i].  Returns true
-// in the last block (after out[] is written and visible to that block).
-__device__ bool finish_reduction(const GmresDev& g, double (*wp)[130], int cnt, int ticket,
-                                 double* out) {
-  __shared__ bool last;
-  __shared__ double gsum[1][130];
-  for (int i = threadIdx.x; i < cnt; i += KT) {
-    double s = 0.0;
-    for (int w = 0; w < KW; ++w) s += wp[w][i];
-    g.part[(int64_t)blockIdx.x * (g.m + 2) + i] = s;
+// ---- staged basis stream -------------------------------------------------------------
+// A step kernel reads the basis rows of its block as a stream of batches (VB vectors x TR
+// rows); thread 0 issues the bulk copies of batch q + 2 while the block multiplies batch q, so
+// FP64 work never waits for a load.  A batch is double-buffered in shared memory with one
+// mbarrier per buffer; every wait is bounded (CPM_ERR_TIMEOUT through the status word).
+constexpr int VB = 8;                   // basis vectors per batch
+constexpr int TR = 1024;                // rows per tile
+constexpr int RU = TR / ST;             // rows per thread in the update pass
+constexpr int WPV = SW / VB;            // warps per vector in the dot pass
+constexpr int RED_LD = 32 * WPV + 1;    // lane partials of one vector, padded
+static_assert(RU * ST == TR && WPV * VB == SW, "batch shape tied to the block shape");
+
+struct StepSmem {
+  double *stage, *ws, *hs, *usum, *red;
+};
+// Dynamic shared memory: stage[2][VB][TR] | ws[chunk] | hs[MAX_UNITS] | usum[MAX_UNITS] |
+// red[MAX_UNITS * RED_LD]
+__device__ __forceinline__ StepSmem step_smem(const GmresDev& g) {
+  extern __shared__ __align__(128) double dsm[];
+  StepSmem s;
+  s.stage = dsm;
+  s.ws = dsm + 2 * VB * TR;
+  s.hs = s.ws + g.chunk;
+  s.usum = s.hs + MAX_UNITS;
+  s.red = s.usum + MAX_UNITS;
+  return s;
+}
+size_t gmres_step_smem_bytes(int chunk) {
+  return sizeof(double) * ((size_t)2 * VB * TR + (size_t)chunk + 2 * MAX_UNITS + (size_t)MAX_UNITS * RED_LD);
+}
+int gmres_max_chunk() { return 4032; }   // rows per block that keep a step kernel within 227 KB
+
+struct VStream {
+  const double* Vb;   // the block's first row of V[0]
+  int64_t ld;
+  int nr, nv;         // rows of the block, vectors 0 .. nv-1
+  int ntile, nbatch, total;
+  double* stage;
+  uint64_t* bar;
+  __device__ int tile(int q) const { return (q / nbatch) % ntile; }
+  __device__ int batch(int q) const { return q % nbatch; }
+  __device__ int rows(int q) const { return min(TR, nr - tile(q) * TR); }
+  __device__ int count(int q) const { return min(VB, nv - batch(q) * VB); }
+  __device__ double* buf(int q) const { return stage + (q & 1) * VB * TR; }
+  // thread 0: bulk copies of batch q (each vector's tile rows, rounded up to 16 bytes: the
+  // vectors are padded to a multiple of 32 doubles, so the extra double is in bounds)
+  __device__ void issue(int q) const {
+    if (q >= total) return;
+    const uint32_t bytes = (uint32_t)((rows(q) * 8 + 15) & ~15);
+    const int i0 = batch(q) * VB, cnt = count(q);
+    mbar_expect_tx(&bar[q & 1], bytes * (uint32_t)cnt);
+    const double* src = Vb + (int64_t)tile(q) * TR;
+    for (int u = 0; u < cnt; ++u) bulk_g2s(buf(q) + u * TR, src + (int64_t)(i0 + u) * ld, bytes, &bar[q & 1]);
   }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&g.ist[ticket], 1) == (int)gridDim.x - 1;
-  __syncthreads();
-  if (!last) return false;
-  __threadfence();
-  // warp w adds value i = w, w + KW, ...: lane l takes blocks l, l + 32, ... (loads issued
-  // together), then a shuffle tree adds the lanes
+  __device__ bool wait(int q) const { return mbar_wait_bounded(&bar[q & 1], (q >> 1) & 1); }
+};
+
+__device__ __forceinline__ VStream make_stream(const GmresDev& g, const double* V, int64_t r0, int nr, int nv,
+                                               int npass, const StepSmem& sm, uint64_t* bar) {
+  VStream v;
+  v.Vb = V + r0;
+  v.ld = g.ld;
+  v.nr = nr;
+  v.nv = nv;
+  v.ntile = max(1, (nr + TR - 1) / TR);
+  v.nbatch = (nv + VB - 1) / VB;
+  v.total = npass * v.ntile * v.nbatch;
+  v.stage = sm.stage;
+  v.bar = bar;
+  return v;
+}
+
+// Start of a step kernel's stream: barriers initialised, the first two batches in flight.
+__device__ __forceinline__ void stream_begin(const VStream& vs, uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    vs.issue(0);
+    vs.issue(1);
+  }
+}
+
+// Bounded wait for batch q by every thread, folded into one block-wide vote.  On failure the
+// status word records the timeout and thread 0 waits (bounded) for the copies still in flight
+// (batches q and q + 1), so that none lands after the block has left.
+__device__ __forceinline__ bool stream_wait(const GmresDev& g, const VStream& vs, int q) {
+  const bool ok = __syncthreads_and(vs.wait(q));
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(g.status, ST_TIMEOUT);
+    for (int r = q; r < min(q + 2, vs.total); ++r) vs.wait(r);
+  }
+  return ok;
+}
+
+// Dot pass over batch q of the stream: warps 2s and 2s+1 own vector i0 + s and take the
+// even / odd 32-row groups of the tile; lane partials x[row] ws[row] accumulate in
+// red[i RED_LD + 32 half + lane] (started at tile 0).  scale_vec >= 0: that vector's values
+// are first multiplied by scale and written back to V.
+__device__ __forceinline__ void dots_batch(const VStream& vs, int q, const StepSmem& sm, int scale_vec,
+                                           double scale, double* Vglob_row0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ld = g.m + 2;
-  for (int i = warp; i < cnt; i += KW) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int b = lane + 32 * u;
-      v[u] = b < g.nblk ? __ldcg(g.part + (int64_t)b * ld + i) : 0.0;
+  const int slot = warp / WPV, half = warp % WPV;
+  const int cnt = vs.count(q);
+  if (slot >= cnt) return;
+  const int t = vs.tile(q), rows = vs.rows(q);
+  const int i = vs.batch(q) * VB + slot;
+  const double* x = vs.buf(q) + slot * TR;
+  const double* ws = sm.ws + t * TR;
+  double a0 = 0.0, a1 = 0.0;
+  if (i == scale_vec) {
+    double* vg = Vglob_row0 + (int64_t)i * vs.ld + (int64_t)t * TR;
+    for (int row = half * 32 + lane; row < rows; row += 32 * WPV) {
+      const double v = x[row] * scale;
+      vg[row] = v;
+      a0 = fma(v, ws[row], a0);
     }
-    double sum = 0.0;
+  } else if (rows == TR) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) sum += v[u];
-    for (int b = lane + 256; b < g.nblk; b += 32) sum += __ldcg(g.part + (int64_t)b * ld + i);
-    sum = warp_sum(sum);
-    if (lane == 0) gsum[0][i] = sum;
+    for (int j = 0; j < TR / (32 * WPV); j += 2) {
+      const int row = (j * WPV + half) * 32 + lane;
+      a0 = fma(x[row], ws[row], a0);
+      a1 = fma(x[row + 32 * WPV], ws[row + 32 * WPV], a1);
+    }
+  } else {
+    for (int row = half * 32 + lane; row < rows; row += 32 * WPV) a0 = fma(x[row], ws[row], a0);
   }
-  __syncthreads();
-  for (int t = threadIdx.x; t < cnt; t += KT) out[t] = gsum[0][t];
-  if (threadIdx.x == 0) g.ist[ticket] = 0;
-  __syncthreads();
-  return true;
+  double* r = sm.red + i * RED_LD + half * 32 + lane;
+  *r = (t == 0 ? 0.0 : *r) + (a0 + a1);
 }
 
-constexpr int RU = 4;                   // rows per thread processed together (loads in flight)
-
-// wp[warp][i] = this warp's share of sum_rows V[i][row] w[row], i <= k, own rows
-__device__ __forceinline__ void block_dots(const GmresDev& g, int k, int64_t r0, int64_t r1,
-                                           double (*wp)[130]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 <= k; i0 += ILP) {
-    double acc[ILP];
+// Update pass over batch q: a[j] += sum_u x_u[row_j] hs[i0 + u] for the thread's rows
+// tid + ST j of the tile.
+__device__ __forceinline__ void update_batch(const VStream& vs, int q, const StepSmem& sm, double (&a)[RU]) {
+  const int cnt = vs.count(q), rows = vs.rows(q), i0 = vs.batch(q) * VB;
+  const double* x = vs.buf(q);
+  if (cnt == VB && rows == TR) {
 #pragma unroll
-    for (int u = 0; u < ILP; ++u) acc[u] = 0.0;
-    for (int64_t base = r0 + threadIdx.x; base < r1; base += RU * KT) {
-      double wv[RU], vv[RU][ILP];
+    for (int u = 0; u < VB; ++u) {
+      const double h = sm.hs[i0 + u];
 #pragma unroll
-      for (int q = 0; q < RU; ++q) {
-        const int64_t row = base + (int64_t)q * KT;
-        wv[q] = row < r1 ? g.w[row] : 0.0;
-#pragma unroll
-        for (int u = 0; u < ILP; ++u)
-          vv[q][u] = (row < r1 && i0 + u <= k) ? g.V[(int64_t)(i0 + u) * g.n + row] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < RU; ++q)
-#pragma unroll
-        for (int u = 0; u < ILP; ++u) acc[u] += vv[q][u] * wv[q];
+      for (int j = 0; j < RU; ++j) a[j] = fma(x[u * TR + threadIdx.x + ST * j], h, a[j]);
     }
-#pragma unroll
-    for (int u = 0; u < ILP; ++u) {
-      const double sum = warp_sum(acc[u]);
-      if (lane == 0 && i0 + u <= k) wp[warp][i0 + u] = sum;
-    }
-  }
-}
-
-// w = A z_k on this block's rows (the operator's second half, the same arithmetic as
-// nbr_sum_kernel), then h1 = V_k^T w
-__global__ void __launch_bounds__(KT) dots_kernel(GmresDev g, const int32_t* __restrict__ nbr, IndirectVec z,
-                                                  const double* __restrict__ vext, double diag, double invh2) {
-  if (cycle_done(g)) return;
-  __shared__ double wp[KW][130];
-  const int k = g.ist[I_K];
-  int64_t r0, r1;
-  block_rows(g, &r0, &r1);
-  const double* zk = z.ptr(0);
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) {
-    const int32_t* nb = nbr + 6 * row;
-    double sn = 0.0;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) sn += vext[__ldg(nb + m)];
-    g.w[row] = diag * zk[row] - invh2 * sn;
-  }
-  block_dots(g, k, r0, r1, wp);
-  __syncthreads();
-  const SL L{g.m};
-  finish_reduction(g, wp, k + 1, I_TICKET + 0, g.st + L.h1());
-}
-
-// w -= V_k h (h at st[h_off]); then either dots with the new w (into h2) or ||w||^2 with
-// the Hessenberg / Givens update in the last block.
-__global__ void __launch_bounds__(KT) update_kernel(GmresDev g, int h_off, int dots) {
-  if (cycle_done(g)) return;
-  __shared__ double hs[130];
-  __shared__ double wp[KW][130];
-  __shared__ double total[130];
-  const int k = g.ist[I_K];
-  for (int i = threadIdx.x; i <= k; i += KT) hs[i] = g.st[h_off + i];
-  __syncthreads();
-  int64_t r0, r1;
-  block_rows(g, &r0, &r1);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t base = r0 + threadIdx.x; base < r1; base += RU * KT) {
-    double a[RU][ILP];
-#pragma unroll
-    for (int q = 0; q < RU; ++q)
-#pragma unroll
-      for (int u = 0; u < ILP; ++u) a[q][u] = 0.0;
-    for (int i0 = 0; i0 <= k; i0 += ILP) {
-      double vv[RU][ILP];
-#pragma unroll
-      for (int q = 0; q < RU; ++q) {
-        const int64_t row = base + (int64_t)q * KT;
-#pragma unroll
-        for (int u = 0; u < ILP; ++u)
-          vv[q][u] = (row < r1 && i0 + u <= k) ? g.V[(int64_t)(i0 + u) * g.n + row] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < RU; ++q)
-#pragma unroll
-        for (int u = 0; u < ILP; ++u) a[q][u] += vv[q][u] * hs[min(i0 + u, k)];
-    }
-#pragma unroll
-    for (int q = 0; q < RU; ++q) {
-      const int64_t row = base + (int64_t)q * KT;
-      double sum = 0.0;
-#pragma unroll
-      for (int u = 0; u < ILP; ++u) sum += a[q][u];
-      if (row < r1) g.w[row] -= sum;
-    }
-  }
-  const SL L{g.m};
-  if (dots) {
-    __syncthreads();
-    block_dots(g, k, r0, r1, wp);
-    __syncthreads();
-    finish_reduction(g, wp, k + 1, I_TICKET + 1, g.st + L.h2());
     return;
   }
-  double s = 0.0;
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) s += g.w[row] * g.w[row];
-  s = warp_sum(s);
-  if (lane == 0) wp[warp][0] = s;
-  __syncthreads();
-  if (!finish_reduction(g, wp, 1, I_TICKET + 2, total)) return;
-  if (threadIdx.x != 0) return;
-  // Hessenberg column k, previous rotations, new rotation, residual estimate
-  double* st = g.st;
-  int* ist = g.ist;
-  const double hn = sqrt(total[0]);
-  for (int i = 0; i <= k; ++i) st[L.H(i, k)] = st[L.h1() + i] + st[L.h2() + i];
-  st[L.H(k + 1, k)] = hn;
-  for (int i = 0; i < k; ++i) {
-    const double c = st[L.cs() + i], sv = st[L.sn() + i];
-    const double a = st[L.H(i, k)], b = st[L.H(i + 1, k)];
-    st[L.H(i, k)] = c * a + sv * b;
-    st[L.H(i + 1, k)] = -sv * a + c * b;
+  for (int u = 0; u < cnt; ++u) {
+    const double h = sm.hs[i0 + u];
+#pragma unroll
+    for (int j = 0; j < RU; ++j) {
+      const int row = threadIdx.x + ST * j;
+      if (row < rows) a[j] = fma(x[u * TR + row], h, a[j]);
+    }
   }
-  const double a = st[L.H(k, k)], b = st[L.H(k + 1, k)];
+}
+
+// out[i] = sum of red[i]'s 64 lane partials for i < nv: warp w takes vectors w, w + SW, ...;
+// lane l adds its two halves, then a shuffle tree (a fixed order, no long chain of dependent
+// FP64 additions, which cost tens of cycles each on this GPU).
+__device__ __forceinline__ void finish_dots(int nv, const StepSmem& sm, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < nv; i += SW) {
+    const double* p = sm.red + i * RED_LD;
+    double s = p[lane] + p[lane + 32];
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+// Sum over the warps of a block of one value per thread (fixed order); valid in thread 0.
+template <int NW>
+__device__ __forceinline__ double block_sum(double v, double* wsum) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < NW ? wsum[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// hs[i] = sum over the grid's blocks of part[b (m+1) + i], i <= k; every block computes the
+// same values in the same order.  Thread (i, slice) adds the blocks slice, slice + nsl, ...
+// with two accumulators, then the nsl slices (a power of two) are added pairwise in a tree.
+__device__ void sum_partials(const GmresDev& g, const double* __restrict__ part, int k, const StepSmem& sm) {
+  const int nv = k + 1;
+  int nsl = 1;
+  while (nsl * 2 * nv <= ST && nsl * 2 <= 64) nsl *= 2;
+  const int t = threadIdx.x;
+  const int i = t % nv, sl = t / nv;
+  if (sl < nsl) {
+    double s0 = 0.0, s1 = 0.0;
+    int b = sl;
+    for (; b + nsl < g.nblk; b += 2 * nsl) {
+      s0 += __ldcg(part + (int64_t)b * (g.m + 1) + i);
+      s1 += __ldcg(part + (int64_t)(b + nsl) * (g.m + 1) + i);
+    }
+    if (b < g.nblk) s0 += __ldcg(part + (int64_t)b * (g.m + 1) + i);
+    sm.red[sl * nv + i] = s0 + s1;
+  }
+  for (int h = nsl / 2; h >= 1; h /= 2) {
+    __syncthreads();
+    if (sl < h) sm.red[sl * nv + i] += sm.red[(sl + h) * nv + i];
+  }
+  __syncthreads();
+  if (t < nv) sm.hs[t] = sm.red[t];
+  __syncthreads();
+}
+
+// w = A z_k on this block's rows (the operator's second half, as in nbr_sum_kernel),
+// V[k] *= s (the scale the previous step left), then partial h1 = V_k^T w.
+__global__ void __launch_bounds__(ST) arn_wdots_kernel(GmresDev g, const int32_t* __restrict__ nbr,
+                                                       const double* __restrict__ vext, int64_t n_nodes,
+                                                       double diag, double invh2) {
+  __shared__ __align__(8) uint64_t bar[2];
+  pdl_launch_next();
+  pdl_wait();
+  const int q = blockIdx.y;
+  const Rhs v = rhs_view(g, q);
+  if (stopped(v)) return;
+  const StepSmem sm = step_smem(g);
+  const int k = v.ist[I_K];
+  const SL L{g.m};
+  const double s = v.st[L.sc() + S_VSCALE];
+  int64_t r0;
+  const int nr = block_rows(g, &r0);
+  const VStream vs = make_stream(g, v.V, r0, nr, k + 1, 1, sm, bar);
+  stream_begin(vs, bar);
+  const double* zk = v.Z + (int64_t)k * g.ld + r0;
+  const double* ve = vext + (int64_t)q * n_nodes;
+  for (int row = threadIdx.x; row < nr; row += ST) {
+    const int32_t* nb = nbr + 6 * (r0 + row);
+    double e[6];
+#pragma unroll
+    for (int mm = 0; mm < 6; ++mm) e[mm] = __ldcg(ve + __ldg(nb + mm));
+    const double sn = ((e[0] + e[1]) + (e[2] + e[3])) + (e[4] + e[5]);
+    const double wv = diag * __ldcg(zk + row) - invh2 * sn;
+    v.w[r0 + row] = wv;
+    sm.ws[row] = wv;
+  }
+  for (int qq = 0; qq < vs.total; ++qq) {
+    if (!stream_wait(g, vs, qq)) return;
+    dots_batch(vs, qq, sm, k > 0 ? k : -1, s, v.V + r0);
+    __syncthreads();
+    if (threadIdx.x == 0) vs.issue(qq + 2);
+  }
+  finish_dots(k + 1, sm, v.p1 + (int64_t)blockIdx.x * (g.m + 1));
+}
+
+// h1 = sum of the partials (block 0 keeps it for the Hessenberg column); w -= V_k h1; partial
+// h2 = V_k^T w.  The stream passes over the basis twice (update, then dots).
+__global__ void __launch_bounds__(ST) arn_upd1_kernel(GmresDev g) {
+  __shared__ __align__(8) uint64_t bar[2];
+  pdl_launch_next();
+  pdl_wait();
+  const int q = blockIdx.y;
+  const Rhs v = rhs_view(g, q);
+  if (stopped(v)) return;
+  const StepSmem sm = step_smem(g);
+  const int k = v.ist[I_K];
+  const SL L{g.m};
+  int64_t r0;
+  const int nr = block_rows(g, &r0);
+  const VStream vs = make_stream(g, v.V, r0, nr, k + 1, 2, sm, bar);
+  stream_begin(vs, bar);
+  sum_partials(g, v.p1, k, sm);
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i <= k; i += ST) v.st[L.h1() + i] = sm.hs[i];
+  const int half = vs.total / 2;
+  double a[RU];
+  for (int qq = 0; qq < vs.total; ++qq) {
+    if (!stream_wait(g, vs, qq)) return;
+    if (qq < half) {
+      if (vs.batch(qq) == 0)
+#pragma unroll
+        for (int j = 0; j < RU; ++j) a[j] = 0.0;
+      update_batch(vs, qq, sm, a);
+      if (vs.batch(qq) == vs.nbatch - 1) {
+        const int t = vs.tile(qq), rows = vs.rows(qq);
+#pragma unroll
+        for (int j = 0; j < RU; ++j) {
+          const int row = threadIdx.x + ST * j;
+          if (row < rows) {
+            const int64_t gr = r0 + (int64_t)t * TR + row;
+            const double wn = __ldcg(v.w + gr) - a[j];
+            v.w[gr] = wn;
+            sm.ws[t * TR + row] = wn;
+          }
+        }
+      }
+    } else {
+      dots_batch(vs, qq, sm, -1, 1.0, nullptr);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) vs.issue(qq + 2);
+  }
+  finish_dots(k + 1, sm, v.p2 + (int64_t)blockIdx.x * (g.m + 1));
+}
+
+// h2 = sum of the partials; w -= V_k h2 into V[k+1] (unnormalised); ||w||^2; the last block
+// adds the norm partials and finishes the step (Hessenberg column h1 + h2 and ||w||, the
+// previous rotations, a new rotation, the residual estimate and the stopping test).
+__global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ bool last;
+  __shared__ double wsum[SW];
+  pdl_wait();
+  const int q = blockIdx.y;
+  const Rhs v = rhs_view(g, q);
+  if (stopped(v)) return;
+  const StepSmem sm = step_smem(g);
+  const int k = v.ist[I_K];
+  const SL L{g.m};
+  int64_t r0;
+  const int nr = block_rows(g, &r0);
+  const VStream vs = make_stream(g, v.V, r0, nr, k + 1, 1, sm, bar);
+  stream_begin(vs, bar);
+  sum_partials(g, v.p2, k, sm);
+  double acc[RU];
+  double ss = 0.0;
+  double* vn = v.V + (int64_t)(k + 1) * g.ld + r0;
+  for (int qq = 0; qq < vs.total; ++qq) {
+    if (!stream_wait(g, vs, qq)) return;
+    if (vs.batch(qq) == 0)
+#pragma unroll
+      for (int j = 0; j < RU; ++j) acc[j] = 0.0;
+    update_batch(vs, qq, sm, acc);
+    if (vs.batch(qq) == vs.nbatch - 1) {
+      const int t = vs.tile(qq), rows = vs.rows(qq);
+#pragma unroll
+      for (int j = 0; j < RU; ++j) {
+        const int row = threadIdx.x + ST * j;
+        if (row < rows) {
+          const int64_t lr = (int64_t)t * TR + row;
+          const double wn = __ldcg(v.w + r0 + lr) - acc[j];
+          vn[lr] = wn;
+          ss = fma(wn, wn, ss);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) vs.issue(qq + 2);
+  }
+  const double bsum = block_sum<SW>(ss, wsum);
+  if (threadIdx.x == 0) {
+    v.p3[blockIdx.x] = bsum;
+    __threadfence();
+    last = atomicAdd(&v.ist[I_TICKET], 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x >= 32) return;
+  double t0 = 0.0, t1 = 0.0;
+  int bb = threadIdx.x;
+  for (; bb + 32 < g.nblk; bb += 64) {
+    t0 += __ldcg(v.p3 + bb);
+    t1 += __ldcg(v.p3 + bb + 32);
+  }
+  if (bb < g.nblk) t0 += __ldcg(v.p3 + bb);
+  const double tot = warp_sum(t0 + t1);
+  double* st = v.st;
+  int* ist = v.ist;
+  // Hessenberg column k (h1 + h2) and the previous rotations, staged in shared memory
+  double* col = sm.red;
+  double* csv = sm.red + MAX_UNITS + 8;
+  double* snv = csv + MAX_UNITS;
+  for (int i = threadIdx.x; i <= k; i += 32) col[i] = __ldcg(st + L.h1() + i) + sm.hs[i];
+  for (int i = threadIdx.x; i < k; i += 32) {
+    csv[i] = __ldcg(st + L.cs() + i);
+    snv[i] = __ldcg(st + L.sn() + i);
+  }
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  ist[I_TICKET] = 0;
+  const double hn = sqrt(tot);
+  // previous rotations applied down the column; the rotated entry i+1 stays in a register
+  double cur = col[0];
+  for (int i = 0; i < k; ++i) {
+    const double c = csv[i], sv = snv[i];
+    const double a = cur, b = col[i + 1];
+    st[L.H(i, k)] = c * a + sv * b;
+    cur = -sv * a + c * b;
+  }
+  const double a = cur, b = hn;
   const double rho = sqrt(a * a + b * b);
   const double c = a / rho, sv = b / rho;
   st[L.cs() + k] = c;
@@ -231,6 +487,7 @@ __global__ void __launch_bounds__(KT) update_kernel(GmresDev g, int h_off, int d
   st[L.g() + k + 1] = -sv * gk;
   st[L.g() + k] = c * gk;
   st[L.sc() + S_HN] = hn;
+  st[L.sc() + S_VSCALE] = 1.0 / hn;
   ist[I_TOTAL] += 1;
   ist[I_KDONE] = k + 1;
   const double est = fabs(st[L.g() + k + 1]);
@@ -240,121 +497,147 @@ __global__ void __launch_bounds__(KT) update_kernel(GmresDev g, int h_off, int d
     ist[I_STATUS] = CPM_ERR_NAN;
     stop = true;
   }
-  if (stop) ist[I_DONE] = 1;
-}
-
-// v_{k+1} = w / ||w||, then the last block advances k
-__global__ void __launch_bounds__(KT) scale_kernel(GmresDev g) {
-  if (cycle_done(g)) return;
-  __shared__ bool last;
-  const SL L{g.m};
-  const int k = g.ist[I_K];
-  const double inv = 1.0 / g.st[L.sc() + S_HN];
-  double* dst = g.V + (int64_t)(k + 1) * g.n;
-  for (int64_t row = (int64_t)blockIdx.x * KT + threadIdx.x; row < g.n; row += (int64_t)gridDim.x * KT)
-    dst[row] = g.w[row] * inv;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    last = atomicAdd(&g.ist[I_TICKET + 3], 1) == (int)gridDim.x - 1;
-    if (last) {
-      g.ist[I_TICKET + 3] = 0;
-      g.ist[I_K] = k + 1;
-    }
+  if (stop) {
+    ist[I_DONE] = 1;
+    ist[I_SLOT] = g.m;                     // later solves of the batch write the spare slot
+    if (atomicSub(&g.ctl[C_LIVE], 1) == 1) g.ctl[C_ALLDONE] = 1;
+  } else {
+    ist[I_K] = k + 1;
+    ist[I_SLOT] = k + 1;
   }
 }
 
 // ---- cycle start / restart ------------------------------------------------------------
-// ||x||^2 over all blocks; the last block applies the begin (which = 0: ||f||) or the
-// convergence test on beta = ||r|| (which = 1).
-__global__ void __launch_bounds__(KT) norm_begin_kernel(GmresDev g, const double* x, double tol,
-                                                        int max_it, int which) {
-  __shared__ double wp[KW][130];
-  __shared__ double total[130];
-  int64_t r0, r1;
-  block_rows(g, &r0, &r1);
+// ||x_q||^2 over the blocks; the last block of right-hand side q applies the begin (which = 0:
+// ||f||, tolerance, iteration limit) or the convergence test on beta = ||r|| (which = 1),
+// which also opens the next cycle of a right-hand side that goes on.
+__global__ void __launch_bounds__(KT) norm_kernel(GmresDev g, const double* __restrict__ x, int64_t x_stride,
+                                                  int which, double tol, int max_it) {
+  __shared__ bool last;
+  __shared__ double wsum[KW];
+  const int q = blockIdx.y;
+  const Rhs v = rhs_view(g, q);
+  const double* xq = x + (int64_t)q * x_stride;
+  int64_t r0;
+  const int nr = block_rows(g, &r0);
   double s = 0.0;
-  for (int64_t row = r0 + threadIdx.x; row < r1; row += KT) s += x[row] * x[row];
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5][0] = s;
+  for (int row = threadIdx.x; row < nr; row += KT) {
+    const double a = xq[r0 + row];
+    s = fma(a, a, s);
+  }
+  const double bsum = block_sum<KW>(s, wsum);
+  if (threadIdx.x == 0) {
+    v.p3[blockIdx.x] = bsum;
+    __threadfence();
+    last = atomicAdd(&v.ist[I_TICKET + 1], 1) == (int)gridDim.x - 1;
+  }
   __syncthreads();
-  if (!finish_reduction(g, wp, 1, I_TICKET + 3, total)) return;
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x >= 32) return;
+  double tot = 0.0;
+  for (int b = threadIdx.x; b < g.nblk; b += 32) tot += __ldcg(v.p3 + b);
+  tot = warp_sum(tot);
   if (threadIdx.x != 0) return;
+  int* ist = v.ist;
+  double* st = v.st;
   const SL L{g.m};
-  const double nrm = sqrt(total[0]);
+  ist[I_TICKET + 1] = 0;
+  const double nrm = sqrt(tot);
+  ist[I_KDONE] = 0;
   if (which == 0) {               // ||f||
-    g.st[L.sc() + S_NF] = nrm;
-    g.st[L.sc() + S_TOL] = tol;
-    g.ist[I_MAXIT] = max_it;
-    g.ist[I_TOTAL] = 0;
-    g.ist[I_STATUS] = RUNNING;
+    st[L.sc() + S_NF] = nrm;
+    st[L.sc() + S_TOL] = tol;
+    ist[I_MAXIT] = max_it;
+    ist[I_TOTAL] = 0;
+    ist[I_STATUS] = RUNNING;
+    ist[I_DONE] = 1;
+    ist[I_SLOT] = g.m;
     return;
   }
   const double beta = nrm;
-  const double nf = g.st[L.sc() + S_NF];
-  g.st[L.sc() + S_BETA] = beta;
-  g.st[L.sc() + S_RELRES] = nf > 0.0 ? beta / nf : 0.0;
-  if (g.ist[I_STATUS] != RUNNING) { g.ist[I_DONE] = 1; return; }
-  if (!isfinite(beta)) {
-    g.ist[I_STATUS] = CPM_ERR_NAN;
-  } else if (nf == 0.0 || beta <= g.st[L.sc() + S_TOL] * nf) {
-    g.ist[I_STATUS] = CPM_OK;
-  } else if (g.ist[I_TOTAL] >= g.ist[I_MAXIT]) {
-    g.ist[I_STATUS] = CPM_ERR_NOT_CONVERGED;
-  } else if (g.ist[I_TOTAL] > 0 && g.st[L.sc() + S_HN] == 0.0) {
-    g.ist[I_STATUS] = CPM_ERR_BREAKDOWN;
+  const double nf = st[L.sc() + S_NF];
+  st[L.sc() + S_BETA] = beta;
+  st[L.sc() + S_RELRES] = nf > 0.0 ? beta / nf : 0.0;
+  if (ist[I_STATUS] == RUNNING) {
+    if (!isfinite(beta)) {
+      ist[I_STATUS] = CPM_ERR_NAN;
+    } else if (nf == 0.0 || beta <= st[L.sc() + S_TOL] * nf) {
+      ist[I_STATUS] = CPM_OK;
+    } else if (ist[I_TOTAL] >= ist[I_MAXIT]) {
+      ist[I_STATUS] = CPM_ERR_NOT_CONVERGED;
+    } else if (ist[I_TOTAL] > 0 && st[L.sc() + S_HN] == 0.0) {
+      ist[I_STATUS] = CPM_ERR_BREAKDOWN;
+    }
   }
-  if (g.ist[I_STATUS] != RUNNING) { g.ist[I_DONE] = 1; return; }
-  for (int i = 0; i <= g.m; ++i) g.st[L.g() + i] = 0.0;
-  g.st[L.g()] = beta;
-  g.ist[I_K] = 0;
-  g.ist[I_KDONE] = 0;
-  g.ist[I_DONE] = 0;
+  if (ist[I_STATUS] != RUNNING) {
+    ist[I_DONE] = 1;
+    ist[I_SLOT] = g.m;
+    return;
+  }
+  for (int i = 0; i <= g.m; ++i) st[L.g() + i] = 0.0;
+  st[L.g()] = beta;
+  st[L.sc() + S_VSCALE] = 1.0;
+  ist[I_K] = 0;
+  ist[I_SLOT] = 0;
+  ist[I_DONE] = 0;
 }
 
-// V[0] = r / beta when a new cycle starts
+// V[0] = r / beta for every right-hand side that opens a cycle
 __global__ void __launch_bounds__(KT) start_basis_kernel(GmresDev g) {
-  if (cycle_done(g)) return;
+  const Rhs v = rhs_view(g, blockIdx.y);
+  if (stopped(v)) return;
   const SL L{g.m};
-  const double inv = 1.0 / g.st[L.sc() + S_BETA];
+  const double inv = 1.0 / v.st[L.sc() + S_BETA];
   for (int64_t row = (int64_t)blockIdx.x * KT + threadIdx.x; row < g.n; row += (int64_t)gridDim.x * KT)
-    g.V[row] = g.r[row] * inv;
+    v.V[row] = v.r[row] * inv;
 }
 
-// y = H[:kd,:kd]^{-1} g[:kd] by one warp (back substitution), then u += Z y
+// y = H[:kd,:kd]^{-1} g[:kd] (back substitution by one warp from a shared-memory copy of the
+// triangle), one block per right-hand side
 __global__ void ysolve_kernel(GmresDev g) {
-  const SL L{g.m};
+  extern __shared__ __align__(16) double hsm[];          // kd x kd, column-major (ld kd)
   __shared__ double ys[129];
-  const int kd = g.ist[I_KDONE];
-  for (int i = threadIdx.x; i < kd; i += 32) ys[i] = g.st[L.g() + i];
-  __syncwarp();
-  for (int i = kd - 1; i >= 0; --i) {
-    double s = 0.0;
-    for (int q = i + 1 + threadIdx.x; q < kd; q += 32) s += g.st[L.H(i, q)] * ys[q];
-    s = warp_sum(s);
-    if (threadIdx.x == 0) ys[i] = (ys[i] - s) / g.st[L.H(i, i)];
+  const Rhs v = rhs_view(g, blockIdx.x);
+  const SL L{g.m};
+  const int kd = v.ist[I_KDONE];
+  if (kd == 0) return;
+  for (int e = threadIdx.x; e < kd * kd; e += blockDim.x) {
+    const int i = e % kd, j = e / kd;
+    hsm[e] = i <= j ? v.st[L.H(i, j)] : 0.0;
+  }
+  for (int i = threadIdx.x; i < kd; i += blockDim.x) ys[i] = v.st[L.g() + i];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  for (int j = kd - 1; j >= 0; --j) {
+    const double yj = ys[j] / hsm[j + j * kd];
+    __syncwarp();
+    for (int i = threadIdx.x; i < j; i += 32) ys[i] = fma(-hsm[i + j * kd], yj, ys[i]);
+    if (threadIdx.x == 0) ys[j] = yj;
     __syncwarp();
   }
-  for (int i = threadIdx.x; i < kd; i += 32) g.st[L.y() + i] = ys[i];
+  for (int i = threadIdx.x; i < kd; i += 32) v.st[L.y() + i] = ys[i];
 }
 
-__global__ void __launch_bounds__(KT) xupdate_kernel(GmresDev g, double* u) {
+// u += Z y (columns 0 .. kd-1), one thread per row
+__global__ void __launch_bounds__(KT) xupdate_kernel(GmresDev g, double* u, int64_t u_stride) {
+  const Rhs v = rhs_view(g, blockIdx.y);
   const SL L{g.m};
-  const int kd = g.ist[I_KDONE];
+  const int kd = v.ist[I_KDONE];
+  if (kd == 0) return;
   __shared__ double ys[128];
-  for (int i = threadIdx.x; i < kd; i += KT) ys[i] = g.st[L.y() + i];
+  for (int i = threadIdx.x; i < kd; i += KT) ys[i] = v.st[L.y() + i];
   __syncthreads();
+  double* uq = u + (int64_t)blockIdx.y * u_stride;
   for (int64_t row = (int64_t)blockIdx.x * KT + threadIdx.x; row < g.n; row += (int64_t)gridDim.x * KT) {
-    double a[ILP];
-#pragma unroll
-    for (int u2 = 0; u2 < ILP; ++u2) a[u2] = 0.0;
-    for (int i0 = 0; i0 < kd; i0 += ILP)
-#pragma unroll
-      for (int u2 = 0; u2 < ILP; ++u2)
-        if (i0 + u2 < kd) a[u2] += g.Z[(int64_t)(i0 + u2) * g.n + row] * ys[i0 + u2];
-    double s = 0.0;
-#pragma unroll
-    for (int u2 = 0; u2 < ILP; ++u2) s += a[u2];
-    u[row] += s;
+    double a0 = 0.0, a1 = 0.0;
+    int i = 0;
+    for (; i + 1 < kd; i += 2) {
+      a0 = fma(v.Z[(int64_t)i * g.ld + row], ys[i], a0);
+      a1 = fma(v.Z[(int64_t)(i + 1) * g.ld + row], ys[i + 1], a1);
+    }
+    if (i < kd) a0 = fma(v.Z[(int64_t)i * g.ld + row], ys[i], a0);
+    uq[row] += a0 + a1;
   }
 }
 
@@ -366,32 +649,61 @@ static unsigned vec_blocks(int64_t n) {
   return (unsigned)(b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b));
 }
 
-cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, double tol, int max_it,
-                               cudaStream_t s) {
-  norm_begin_kernel<<<g.nblk, KT, 0, s>>>(g, f, tol, max_it, 0);
+static size_t ysolve_smem(int m) { return sizeof(double) * (size_t)m * m; }
+
+cudaError_t gmres_prepare(int chunk, int m) {
+  const int step = (int)gmres_step_smem_bytes(chunk);
+  cudaError_t e = cudaFuncSetAttribute(arn_wdots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(arn_upd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(arn_upd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(ysolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysolve_smem(m));
+  return e;
+}
+
+// kernel launch with programmatic stream serialisation (the kernel waits on its predecessor
+// with griddepcontrol.wait)
+template <typename... Args>
+static cudaError_t launch_pdl(void (*kern)(Args...), dim3 grid, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(ST);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, int64_t f_stride, double tol, int max_it,
+                               int nr, cudaStream_t s) {
+  norm_kernel<<<dim3(g.nblk, nr), KT, 0, s>>>(g, f, f_stride, 0, tol, max_it);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cgs2_and_givens(const GmresDev& g, const OperatorDev& op, IndirectVec z, const double* vext,
-                                   cudaStream_t s) {
-  const SL L{g.m};
-  dots_kernel<<<g.nblk, KT, 0, s>>>(g, op.nbr, z, vext, op.diag, op.invh2);
-  update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h1(), 1);
-  update_kernel<<<g.nblk, KT, 0, s>>>(g, L.h2(), 0);
-  scale_kernel<<<vec_blocks(g.n), KT, 0, s>>>(g);
-  return cudaGetLastError();
+cudaError_t launch_arnoldi_step(const GmresDev& g, const OperatorDev& op, const double* vext, int nr,
+                                cudaStream_t s) {
+  const size_t smem = gmres_step_smem_bytes(g.chunk);
+  const dim3 grid(g.nblk, nr);
+  cudaError_t e = launch_pdl(arn_wdots_kernel, grid, smem, s, g, op.nbr, vext, op.n_nodes, op.diag, op.invh2);
+  if (e == cudaSuccess) e = launch_pdl(arn_upd1_kernel, grid, smem, s, g);
+  if (e == cudaSuccess) e = launch_pdl(arn_upd2_kernel, grid, smem, s, g);
+  return e;
 }
 
-cudaError_t launch_gmres_restart_update(const GmresDev& g, double* u, cudaStream_t s) {
-  ysolve_kernel<<<1, 32, 0, s>>>(g);
-  xupdate_kernel<<<vec_blocks(g.n), KT, 0, s>>>(g, u);
+cudaError_t launch_gmres_restart_update(const GmresDev& g, double* u, int64_t u_stride, int nr, cudaStream_t s) {
+  ysolve_kernel<<<nr, 128, ysolve_smem(g.m), s>>>(g);
+  xupdate_kernel<<<dim3(vec_blocks(g.n), nr), KT, 0, s>>>(g, u, u_stride);
   return cudaGetLastError();
 }
 
 // after r = f - A u: beta, convergence decision, and V[0] = r / beta for the next cycle
-cudaError_t launch_gmres_residual_check(const GmresDev& g, cudaStream_t s) {
-  norm_begin_kernel<<<g.nblk, KT, 0, s>>>(g, g.r, 0.0, 0, 1);
-  start_basis_kernel<<<vec_blocks(g.n), KT, 0, s>>>(g);
+cudaError_t launch_gmres_residual_check(const GmresDev& g, int nr, cudaStream_t s) {
+  norm_kernel<<<dim3(g.nblk, nr), KT, 0, s>>>(g, g.r, g.ld, 1, 0.0, 0);
+  start_basis_kernel<<<dim3(vec_blocks(g.n), nr), KT, 0, s>>>(g);
   return cudaGetLastError();
 }
 

@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
     if (skip) return t.n_items;
     return (int)atomicAdd(&t.sync[0], 1u);
   };
+  const uint64_t l2_pol = l2_evict_first_policy();   // factor tiles are read once per launch
   auto issue_load = [&](const Item& e, int l) {
     const int st = lc % NSTAGE;
     unsigned char* dst = smem + (size_t)st * STAGE;
@@ -202,11 +203,11 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
     if (tq >= 0) {
       const int q = e.q0 + tq;
       const int J = e.bwd ? e.jb - q : e.jb + q;
-      bulk_g2s(dst, tiles + tile_base(m, e.I, J), STAGE, &bar[st]);
+      bulk_g2s_hint(dst, tiles + tile_base(m, e.I, J), STAGE, &bar[st], l2_pol);
     } else {
       const int64_t trow = (m.row_off >> 6) + e.I;
       const unsigned char* it = (const unsigned char*)(inv + (trow * 2 + e.bwd) * (int64_t)TILE_ELEMS);
-      bulk_g2s(dst, it + (size_t)piece * STAGE, STAGE, &bar[st]);
+      bulk_g2s_hint(dst, it + (size_t)piece * STAGE, STAGE, &bar[st], l2_pol);
     }
     ++lc;
   };
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
       const int g = t.gather[ro + tid];
       if (g >= 0)
 #pragma unroll
-        for (int q = 0; q < NR; ++q) rhs[q] = (C)r_in.ptr(q)[g];
+        for (int q = 0; q < NR; ++q) rhs[q] = (C)r_in.load(q, g);
     }
     // tagged words of the solved piece multiplying off-diagonal tile l of this item
     auto ywords = [&](int l, int q) {

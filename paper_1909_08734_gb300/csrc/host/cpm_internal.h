@@ -74,6 +74,7 @@ struct Band {
   mutable void* d_pencil = nullptr;
   mutable void* d_wts = nullptr;
   mutable void* d_nbr = nullptr;
+  mutable void* d_wt2 = nullptr;   // (P^2 + P) x N tensor weights wy_b wz_c and wx_a (device)
   mutable int d_device = -1;
 };
 

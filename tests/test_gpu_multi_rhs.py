@@ -59,3 +59,32 @@ def test_multi_rhs_stationary_is_bitwise_single_rhs(bp):
         r1 = G.oras_stationary_solve(pc, Fd[q].contiguous(), u, tol=1e-8, max_it=500)[0]
         assert r1["iterations"] == res[q]["iterations"]
         assert torch.equal(u, U[q]), q
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("nrhs,restart,use_graph", [(3, 50, True), (8, 6, True), (5, 6, False)])
+def test_lock_step_gmres_is_bitwise_single_rhs(bp, prec, nrhs, restart, use_graph):
+    # FGMRES over several right-hand sides in lock step (one solve launch per iteration for
+    # all of them) gives every right-hand side exactly its single-rhs iterates: the same
+    # iteration count, residual and solution bits, also when right-hand sides stop in
+    # different restart cycles (restart 6) and with a zero right-hand side in the batch.
+    band, part = bp
+    pc = G.oras_setup(band, part, 10.0, "oras", 4.0, 40.0, prec)
+    n = pc.n_active
+    F = np.stack([random_vector(n, 300 + q) * (1.0 + 3.0 * q) for q in range(nrhs)])
+    F[1] *= 0.0
+    if nrhs > 2:
+        F[2] = F[0] + 1e-3 * F[2]                   # a near-duplicate converging at a similar step
+    Fd = torch.tensor(F, dtype=torch.float64, device="cuda")
+    U = torch.zeros_like(Fd)
+    res = G.cpm_gmres_solve(pc, Fd.view(-1), U.view(-1), nrhs=nrhs, tol=1e-9, restart=restart,
+                            max_it=600, use_graph=use_graph)
+    assert all(r["status"] == 0 for r in res), res
+    assert res[1]["iterations"] == 0 and torch.count_nonzero(U[1]).item() == 0
+    for q in range(nrhs):
+        u = torch.zeros(n, dtype=torch.float64, device="cuda")
+        r1 = G.cpm_gmres_solve(pc, Fd[q].contiguous(), u, tol=1e-9, restart=restart, max_it=600,
+                               use_graph=use_graph)[0]
+        assert r1["iterations"] == res[q]["iterations"], (q, r1, res[q])
+        assert r1["relres"] == res[q]["relres"], q
+        assert torch.equal(u, U[q]), q
