@@ -137,6 +137,121 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# ---- the oracle with its local solves on all host cores (cpu_baseline and reference arm) ----
+def _oracle_worker(conn, r_name, z_name, n, lps):
+    """One process of the pool: factors its share of the oracle's local matrices with the
+    oracle's own SciPy SuperLU, then answers apply requests (r and z in shared memory; each
+    worker writes only the disjoint sets of its subdomains)."""
+    from multiprocessing import shared_memory
+    import scipy.sparse.linalg as spla
+    rs = shared_memory.SharedMemory(name=r_name)
+    zs = shared_memory.SharedMemory(name=z_name)
+    r = np.ndarray((n,), dtype=np.float64, buffer=rs.buf)
+    z = np.ndarray((n,), dtype=np.float64, buffer=zs.buf)
+    facs = [spla.splu(lp.A.tocsc()) for lp in lps]
+    conn.send("ready")
+    while conn.recv() is not None:
+        for lp, fac in zip(lps, facs):
+            e = fac.solve(lp.rhs(r))
+            z[lp.own_global] = e[lp.own_local]
+        conn.send(1)
+    del r, z
+    rs.close()
+    zs.close()
+
+
+class OraclePool:
+    """The oracle's Schwarz preconditioner (oracle.schwarz.Schwarz.apply) with its local
+    solves spread over `workers` spawned processes; the Krylov iteration stays the oracle's."""
+
+    def __init__(self, prob, workers: int):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        n = prob.band.n_active
+        self.n = n
+        self.rs = shared_memory.SharedMemory(create=True, size=8 * n)
+        self.zs = shared_memory.SharedMemory(create=True, size=8 * n)
+        self.r = np.ndarray((n,), dtype=np.float64, buffer=self.rs.buf)
+        self.z = np.ndarray((n,), dtype=np.float64, buffer=self.zs.buf)
+        # largest subdomains first, each to the least loaded worker (cost ~ n_j^1.5)
+        loads, shares = [0.0] * workers, [[] for _ in range(workers)]
+        for j in sorted(range(len(prob.lps)), key=lambda j: -prob.lps[j].n):
+            w = int(np.argmin(loads))
+            shares[w].append(prob.lps[j])
+            loads[w] += prob.lps[j].n ** 1.5
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for share in shares:
+            a, b = ctx.Pipe()
+            pr = ctx.Process(target=_oracle_worker, args=(b, self.rs.name, self.zs.name, n, share), daemon=True)
+            pr.start()
+            self.conns.append(a)
+            self.procs.append(pr)
+        for c in self.conns:
+            c.recv()
+
+    def apply(self, r):
+        self.r[:] = r
+        for c in self.conns:
+            c.send(1)
+        for c in self.conns:
+            c.recv()
+        return self.z.copy()
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for pr in self.procs:
+            pr.join(timeout=10)
+        del self.r, self.z
+        self.rs.close()
+        self.rs.unlink()
+        self.zs.close()
+        self.zs.unlink()
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_baseline(wl, full_solves: int = 1, one_core: bool = True):
+    """The CPU FP64 oracle on this host: full FGMRES solves with the local solves on all cores
+    (spawned process pool), and one full single-process solve.  Returns (summary, x)."""
+    from oracle import krylov, problems
+    t = time.time()
+    P = problems.setup_workload(wl)
+    setup = time.time() - t
+    cores = _host_cores()
+    out = {"kind": "oracle", "unit": "solves/s", "oracle_setup_s": round(setup, 2)}
+    x = None
+    if one_core:
+        t = time.time()
+        res = problems.solve(P, P.f, wl.tol, wl.restart, wl.max_it)
+        dt = time.time() - t
+        x = res.x
+        out["one_core"] = {"value": round(1.0 / dt, 5), "cores": 1, "iterations": res.iterations,
+                           "sample": f"one full FGMRES({wl.restart}) solve to {wl.tol:g}"}
+    pool = OraclePool(P, cores)
+    try:
+        times = []
+        for _ in range(full_solves):
+            t = time.time()
+            res = krylov.fgmres(lambda v: P.A @ v, pool.apply, P.f, wl.tol, wl.restart, wl.max_it)
+            times.append(time.time() - t)
+        x = res.x if x is None else x
+    finally:
+        pool.close()
+    out.update({"value": round(1.0 / statistics.mean(times), 5), "cores": cores, "iterations": res.iterations,
+                "sample": f"{full_solves} full FGMRES({wl.restart}) solve(s) to {wl.tol:g} of {wl.name}, "
+                          f"local SuperLU solves on {cores} processes (spawn), Krylov and operator in the "
+                          f"parent; oracle set-up of {setup:.1f} s excluded",
+                "times_s": [round(v, 3) for v in times]})
+    return out, x, P
+
+
 def run_kernel_only(args):
     """Set up one preconditioner and launch only the batched solve (for profiler captures)."""
     import torch
@@ -162,10 +277,45 @@ def run_kernel_only(args):
                          if k in ("factor_bytes", "sum_n2", "n_sub", "tile_rows", "solve_offdiag_tiles")}}))
 
 
+SURFACE_LABEL = {"sphere": "unit sphere", "torus": "torus", "trimesh": "perturbed icosphere (triangles)"}
+RHS_LABEL = {"xyz": "f=(c+12)xyz at closest points", "torus_modes": "16 seeded trig modes in the torus angles",
+             "ambient_modes": "8 seeded ambient cosine modes"}
+DTYPE = {"fp32": "f32 local factors and solves + f64 Krylov/operator",
+         "bf16": "bf16 local factors (f32 solves) + f64 Krylov/operator",
+         "fp64": "f64 local factors, solves, Krylov and operator"}
+
+
+def _build_band(G, wl):
+    from workloads import surface_mesh
+    mesh = surface_mesh(wl)
+    if mesh is None:
+        return G.cpm_build_band(wl.surface, wl.R, wl.r, wl.h, wl.p)
+    return G.cpm_build_band(wl.surface, wl.R, wl.r, wl.h, wl.p, verts=mesh[0], tris=mesh[1])
+
+
+def _workload_config(wl, info, n, world, alg_bytes, vec_bytes):
+    cfg = {"workload": wl.name, "surface": SURFACE_LABEL.get(wl.surface, wl.surface), "h": wl.h, "p": wl.p,
+           "c": wl.c, "N_A": n, "n_sub": wl.n_sub, "overlap": wl.n_overlap, "method": wl.method.upper(),
+           "krylov": f"FGMRES({wl.restart})", "tol": wl.tol, "factor_precision": wl.precision,
+           "factor_bytes": info["factor_bytes"],
+           "l2": "inputs larger than L2: every iteration streams %.2f GB of factor tiles"
+                 % ((alg_bytes - vec_bytes) / 1e9),
+           "parallelism": f"replicas x{world}"}
+    if wl.method == "oras":
+        cfg.update({"alpha": wl.alpha, "alpha_x": wl.alpha_x})
+    if wl.surface == "torus":
+        cfg.update({"R": wl.R, "r": wl.r})
+    if wl.surface == "trimesh":
+        cfg.update({"triangles": 20 * 4 ** wl.mesh_level, "radial_noise": wl.mesh_amp})
+    if wl.weight_seed is not None:
+        cfg["leaf_weights"] = f"seeded uniform [256, 1024] (seed {wl.weight_seed})"
+    return cfg
+
+
 def run_native(args):
     import torch
     import paper_1909_08734_gb300 as G
-    from workloads import WORKLOADS, rhs
+    from workloads import WORKLOADS, leaf_weights, rhs
 
     world, rank, local = _dist()
     torch.cuda.set_device(local)
@@ -174,17 +324,16 @@ def run_native(args):
         dist.init_process_group("nccl")
     wl = WORKLOADS[args.workload]
     dev = torch.device("cuda", local)
+    head = wl.precision                         # the workload's factor precision is the headline
+    precs = [head] + [p for p in ("fp32", "bf16", "fp64") if p != head and not (args.no_fp64 and p == "fp64")]
 
     t0 = time.time()
-    band = G.cpm_build_band(wl.surface, wl.R, wl.r, wl.h, wl.p)
-    from workloads import leaf_weights
+    band = _build_band(G, wl)
     part = G.cpm_partition(band, wl.n_sub, leaf_weights(wl.n_sub, wl.weight_seed), wl.n_overlap)
     host_setup_s = time.time() - t0
     cp = band.info()["cp"]
-    pcs = {}
-    setup_s = {}
-    schedules = {}
-    for prec in ["fp32", "bf16", "fp64"] if not args.no_fp64 else ["fp32", "bf16"]:
+    pcs, setup_s, schedules = {}, {}, {}
+    for prec in precs:
         torch.cuda.synchronize()
         t = time.time()
         pcs[prec] = G.oras_setup(band, part, wl.c, wl.method, wl.alpha, wl.alpha_x, prec)
@@ -193,32 +342,31 @@ def run_native(args):
         t = time.time()
         schedules[prec] = G.oras_autotune(pcs[prec])
         setup_s[prec + "_autotune"] = time.time() - t
-    pc = pcs["fp32"]
+    pc = pcs[head]
     n = pc.n_active
     f_host = rhs(wl, cp[:n])
     f = torch.tensor(f_host, dtype=torch.float64, device=dev)
     u = torch.zeros_like(f)
     stream = torch.cuda.current_stream(dev)
 
-    def solve(p, ff, uu):
-        return G.cpm_gmres_solve(p, ff, uu, restart=wl.restart, tol=wl.tol, max_it=wl.max_it,
+    def solve(p, ff, uu, nrhs=1):
+        return G.cpm_gmres_solve(p, ff, uu, nrhs=nrhs, restart=wl.restart, tol=wl.tol, max_it=wl.max_it,
                                  stream=stream)
 
-    def timed_solves(p, k, w):
+    def timed_solves(p, k, w, ff=f, uu=u, nrhs=1):
         for _ in range(w):
-            solve(p, f, u)
+            solve(p, ff, uu, nrhs)
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
         res = []
         ev[0].record(stream)
         for i in range(k):
-            res.append(solve(p, f, u))
+            res.append(solve(p, ff, uu, nrhs))
             ev[i + 1].record(stream)
         torch.cuda.synchronize()
-        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(k)]
-        return per, res
+        return [ev[i].elapsed_time(ev[i + 1]) for i in range(k)], res
 
-    # ---- headline: mixed (FP32 factors) ----
+    # ---- headline: the workload's factor precision, factors resident ----
     for _ in range(args.warmup):
         solve(pc, f, u)
     torch.cuda.synchronize()
@@ -245,75 +393,119 @@ def run_native(args):
     launches = pc.info()["kernel_launches"] - launches0
     iters = results[-1][0]["iterations"]
     relres = results[-1][0]["relres"]
+    u_head = u.clone()
+    head_ms = statistics.median(per_step)
 
-    # ---- solution error of the mixed path against the FP64 path ----
-    extra = {}
-    if "fp64" in pcs:
-        u64 = torch.zeros_like(f)
-        per64, res64 = timed_solves(pcs["fp64"], max(3, args.steps // 2), 1)
-        solve(pcs["fp64"], f, u64)
-        solve(pc, f, u)
-        torch.cuda.synchronize()
-        diff = (torch.linalg.norm(u - u64) / torch.linalg.norm(u64)).item()
-        extra["fp64"] = {"solves_per_s": 1e3 / statistics.mean(per64),
-                         "ms_p50": statistics.median(per64), "iterations": res64[-1][0]["iterations"],
-                         "relres": res64[-1][0]["relres"], "setup_s": setup_s["fp64"],
-                         "setup_ms_factor": pcs["fp64"].info()["setup_ms_factor"]}
-        extra["mixed_vs_fp64_solution_rel_diff"] = diff
-        extra["mixed_speedup_vs_fp64_solve"] = extra["fp64"]["ms_p50"] / statistics.median(per_step)
+    # ---- the other factor precisions on the same operators ----
+    extra, sols = {}, {head: u_head}
+    for prec in precs[1:]:
+        uu = torch.zeros_like(f)
+        per, res = timed_solves(pcs[prec], max(3, args.steps // 2), 1, f, uu)
+        sols[prec] = uu.clone()
+        extra[prec] = {"solves_per_s": 1e3 / statistics.mean(per), "ms_p50": statistics.median(per),
+                       "iterations": res[-1][0]["iterations"], "relres": res[-1][0]["relres"],
+                       "setup_s": setup_s[prec], "setup_ms_factor": pcs[prec].info()["setup_ms_factor"]}
+    if "fp64" in pcs and head != "fp64":
+        u64 = sols["fp64"]
+        extra["mixed_vs_fp64_solution_rel_diff"] = (torch.linalg.norm(u_head - u64) / torch.linalg.norm(u64)).item()
+        extra["mixed_speedup_vs_fp64_solve"] = extra["fp64"]["ms_p50"] / head_ms
         extra["mixed_speedup_vs_fp64_setup_plus_solve"] = (
-            (setup_s["fp64"] + extra["fp64"]["ms_p50"] / 1e3) /
-            (setup_s["fp32"] + statistics.median(per_step) / 1e3))
+            (setup_s["fp64"] + extra["fp64"]["ms_p50"] / 1e3) / (setup_s[head] + head_ms / 1e3))
         # the metric reported twice: solve with factors resident (value) and set-up + solve
         extra["setup_plus_solve_s"] = {
-            "fp32": round(host_setup_s + setup_s["fp32"] + statistics.median(per_step) / 1e3, 4),
+            head: round(host_setup_s + setup_s[head] + head_ms / 1e3, 4),
             "fp64": round(host_setup_s + setup_s["fp64"] + extra["fp64"]["ms_p50"] / 1e3, 4)}
-    per16, res16 = timed_solves(pcs["bf16"], max(3, args.steps // 2), 1)
-    extra["bf16"] = {"solves_per_s": 1e3 / statistics.mean(per16), "ms_p50": statistics.median(per16),
-                     "iterations": res16[-1][0]["iterations"], "relres": res16[-1][0]["relres"],
-                     "setup_s": setup_s["bf16"]}
 
-    # ---- roofline of the dominant kernel: the batched restrict / LU solve / prolong ----
+
+    # ---- rooflines: the batched solve (dominant), the operator apply, the Arnoldi kernels ----
     info = pc.info()
     r = torch.randn(n, dtype=torch.float64, device=dev)
     z = torch.empty_like(r)
 
-    def apply_time(p, nl=20):
+    def event_ms(fn, nl):
         for _ in range(3):
-            G.oras_apply(p, r, z, stream=stream)
+            fn()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(nl):
-            G.oras_apply(p, r, z, stream=stream)
+            fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        G.oras_check_status(p)
         return e0.elapsed_time(e1) / nl
 
-    apply_ms = apply_time(pc)
+    def apply_time(p, nl=20):
+        ms = event_ms(lambda: G.oras_apply(p, r, z, stream=stream), nl)
+        G.oras_check_status(p)
+        return ms
+
+    fp64_peak, fp64_dep_cycles = G.cpm_probe_fp64(2 * torch.cuda.get_device_properties(dev).multi_processor_count,
+                                                  1024, 8, 4096, latency=True)
+    peak, peak_kind = _peaks()
     # bytes one application must stream: the off-diagonal factor tiles inside the tile
     # envelope (storage precision), two inverted diagonal blocks per tile row (compute
     # precision), the restricted residual reads and the prolonged writes
     tiles_off, tiles_inv = info["solve_offdiag_tiles"] * 4096, 2 * info["tile_rows"] * 4096
     vec_bytes = 8 * info["sum_sigma"] + 8 * n
-    alg_bytes = 4 * tiles_off + 4 * tiles_inv + vec_bytes
-    peak, peak_kind = _peaks()
-    ms16 = apply_time(pcs["bf16"])
-    b16 = 2 * tiles_off + 4 * tiles_inv + vec_bytes
-    extra["bf16"]["solve_kernel"] = {"launch_ms": round(ms16, 4), "achieved_gbs": round(b16 / ms16 / 1e6, 1),
-                                     "frac": round(b16 / ms16 / 1e6 / peak, 4)}
-    if "fp64" in pcs:
-        ms64 = apply_time(pcs["fp64"], 5)
-        b64 = 8 * tiles_off + 8 * tiles_inv + vec_bytes
-        extra["fp64"]["solve_kernel"] = {
-            "launch_ms": round(ms64, 4), "achieved_gbs": round(b64 / ms64 / 1e6, 1),
-            "fp64_tflops": round(2 * (tiles_off + tiles_inv) / ms64 / 1e9, 3), "bound": "fp64 alu"}
-    achieved = alg_bytes / (apply_ms / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": _profiled_traffic(),
-                "kernel": "trsv_kernel<float,float>", "launch_ms": round(apply_ms, 4),
-                "algorithmic_bytes": alg_bytes, "peak_source": peak_kind}
+    store = {"fp32": 4, "bf16": 2, "fp64": 8}
+    comp = {"fp32": 4, "bf16": 4, "fp64": 8}
+    solve_ms = {}
+    for prec in precs:
+        ms = apply_time(pcs[prec], 20 if prec != "fp64" else 5)
+        solve_ms[prec] = ms
+        b = store[prec] * tiles_off + comp[prec] * tiles_inv + vec_bytes
+        k = {"launch_ms": round(ms, 4), "achieved_gbs": round(b / ms / 1e6, 1), "frac_hbm": round(b / ms / 1e6 / peak, 4),
+             "algorithmic_bytes": b}
+        if prec == "fp64":
+            k.update({"fp64_tflops": round(2 * (tiles_off + tiles_inv) / ms / 1e9, 3), "bound": "fp64 alu",
+                      "frac_fp64": round(2 * (tiles_off + tiles_inv) / ms / 1e9 / fp64_peak, 4)})
+        if prec == head:
+            head_bytes = b
+        else:
+            extra[prec]["solve_kernel"] = k
+    apply_ms = solve_ms[head]
+    if head == "fp64":
+        fl = 2 * (tiles_off + tiles_inv)
+        achieved = fl / (apply_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                    "frac": round(achieved / fp64_peak, 4), "traffic": None, "kernel": "trsv_kernel<double,double>",
+                    "launch_ms": round(apply_ms, 4), "algorithmic_flops": fl,
+                    "peak_source": "measured FP64 FMA probe (cpm_probe_fp64), this run"}
+    else:
+        achieved = head_bytes / (apply_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4),
+                    "traffic": _profiled_traffic() if (head == "fp32" and wl.name == "sphere_h0025") else None,
+                    "kernel": "trsv_kernel<%s>" % ("float,float" if head == "fp32" else "bf16,float"),
+                    "launch_ms": round(apply_ms, 4), "algorithmic_bytes": head_bytes, "peak_source": peak_kind}
+    # operator apply y = A x (FP64, matrix-free): extension values at every band node, then the
+    # 7-point sums; algorithmic work per the scope table: 2 (p+1)^3 (N_A + N_G) + 8 N_A flops and
+    # 8 N_A (x) + 8 N_A (y) + 24 (N_A + N_G) + 4 (p+1)^2 (N_A + N_G) + 24 N_A bytes
+    NN = info["n_nodes"]
+    P3, P2 = (wl.p + 1) ** 3, (wl.p + 1) ** 2
+    y = torch.empty_like(r)
+    op_ms = event_ms(lambda: G.cpm_op_apply(pc, r, y, stream=stream), 20)
+    op_flops = 2 * P3 * NN + 8 * n
+    op_bytes = 8 * n + 8 * n + 24 * NN + 4 * P2 * NN + 24 * n
+    impl_fma = (P3 + wl.p + 1) * NN + 8 * n            # FP64 operations the kernels issue
+    iter_ms = head_ms / max(1, iters)
+    arn_ms = iter_ms - apply_ms - op_ms
+    kbar = (iters - 1) / 2.0 if iters < wl.restart else (wl.restart - 1) / 2.0
+    arn_flops = 8 * (kbar + 1) * n + 10 * n                # CGS2 at the mean step + w and the norm
+    extra["operator_apply"] = {
+        "launch_ms": round(op_ms, 4), "bound": "alu",
+        "fp64_tflops_algorithmic": round(op_flops / op_ms / 1e9, 4),
+        "fp64_tflops_issued": round(2 * impl_fma / op_ms / 1e9, 4),
+        "frac_fp64_issued": round(2 * impl_fma / op_ms / 1e9 / fp64_peak, 4),
+        "achieved_gbs_algorithmic": round(op_bytes / op_ms / 1e6, 1),
+        "frac_hbm_algorithmic": round(op_bytes / op_ms / 1e6 / peak, 4)}
+    extra["iteration_breakdown_ms"] = {
+        "iteration": round(iter_ms, 4), "solve_kernel": round(apply_ms, 4), "operator_apply": round(op_ms, 4),
+        "arnoldi_cgs2_givens_and_per_solve": round(arn_ms, 4),
+        "arnoldi_fp64_tflops": round(arn_flops / (arn_ms / 1e3) / 1e12, 4) if arn_ms > 0 else None,
+        "arnoldi_frac_fp64": round(arn_flops / (arn_ms / 1e3) / 1e12 / fp64_peak, 4) if arn_ms > 0 else None}
+    extra["fp64_peak"] = {"fma_tflop_s": round(fp64_peak, 4), "dependent_fma_cycles": round(fp64_dep_cycles, 1),
+                          "source": "cpm_probe_fp64 in this run (bench.py --peaks sweeps it)"}
 
     # ---- end to end through the C ABI with host buffers ----
     f_pin = torch.tensor(f_host, dtype=torch.float64).pin_memory()
@@ -339,50 +531,54 @@ def run_native(args):
     e2e = {"value": round(world * 1e3 / e2e_ms, 3), "unit": "solves/s",
            "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n}
 
-    # ---- several right-hand sides per streamed factor tile (after every single-rhs timing:
-    # the first multi-rhs launch grows the solve's tagged-word buffers) ----
-    r8 = torch.randn(8 * n, dtype=torch.float64, device="cuda")
+    # ---- several right-hand sides: one solve launch for 8 per iteration, and FGMRES over 8
+    # right-hand sides in lock step (after every single-rhs timing: the first multi-rhs launch
+    # grows the solve's tagged-word buffers) ----
+    r8 = torch.randn(8 * n, dtype=torch.float64, device=dev)
     z8 = torch.empty_like(r8)
-    for _ in range(3):
-        G.oras_apply(pc, r8, z8, nrhs=8, stream=stream)
-    m0 = torch.cuda.Event(enable_timing=True)
-    m1 = torch.cuda.Event(enable_timing=True)
-    m0.record(stream)
-    for _ in range(10):
-        G.oras_apply(pc, r8, z8, nrhs=8, stream=stream)
-    m1.record(stream)
-    torch.cuda.synchronize()
+    ms8 = event_ms(lambda: G.oras_apply(pc, r8, z8, nrhs=8, stream=stream), 10)
     G.oras_check_status(pc)
-    ms8 = m0.elapsed_time(m1) / 10
     extra["multi_rhs_apply"] = {"nrhs": 8, "launch_ms": round(ms8, 4), "ms_per_rhs": round(ms8 / 8, 4),
                                 "speedup_per_rhs_vs_single": round(8 * apply_ms / ms8, 2)}
+    from workloads import smooth_rhs
+    F8 = torch.tensor(smooth_rhs(cp[:n], 77, 8).T.copy(), dtype=torch.float64, device=dev).reshape(-1)
+    U8 = torch.zeros_like(F8)
+    lock = {}
+    for prec in [head] + (["fp64"] if "fp64" in pcs and head != "fp64" else []):
+        per8, res8 = timed_solves(pcs[prec], 3, 1, F8, U8, nrhs=8)
+        lock[prec] = {"ms_per_batch_p50": round(statistics.median(per8), 3),
+                      "solves_per_s": round(8e3 / statistics.median(per8), 3),
+                      "iterations": [q["iterations"] for q in res8[-1]],
+                      "max_relres": max(q["relres"] for q in res8[-1])}
+    if len(lock) == 2:
+        lock["mixed_speedup_vs_fp64"] = round(lock[head]["solves_per_s"] / lock["fp64"]["solves_per_s"], 3)
+    extra["lock_step_8_rhs"] = lock
 
-    # ---- CPU baseline: the oracle, rank 0 at N = 1 only ----
+    # ---- CPU baseline: the oracle, rank 0 at N = 1 only; and the solution errors against it ----
     cpu_baseline = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_baseline = oracle_solve_rate(wl, sample_iterations=None)
+        cpu_baseline, x_or, _ = oracle_baseline(wl, full_solves=1, one_core=True)
+        xo = torch.tensor(x_or, dtype=torch.float64, device=dev)
+        extra["solution_rel_err_vs_oracle"] = {
+            prec: (torch.linalg.norm(sols[prec] - xo) / torch.linalg.norm(xo)).item() for prec in sols}
+        extra["solution_rel_err_vs_oracle"]["note"] = f"both sides solved to {wl.tol:g} relative residual"
 
+    info = pc.info()
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total_ms / args.steps, 3),
-        "ms_p50": round(statistics.median(per_step), 3),
+        "ms_p50": round(head_ms, 3),
         "ms_p99": round(float(np.percentile(per_step, 99)), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 local factors and solves + f64 Krylov/operator",
-        "data": "synthetic (seeded workloads module; unit sphere, f=(c+12)xyz at closest points)",
-        "config": {"workload": wl.name, "surface": "unit sphere", "h": wl.h, "p": wl.p, "c": wl.c,
-                   "N_A": n, "n_sub": wl.n_sub, "overlap": wl.n_overlap, "method": "ORAS",
-                   "alpha": wl.alpha, "alpha_x": wl.alpha_x, "krylov": f"FGMRES({wl.restart})",
-                   "tol": wl.tol, "factor_precision": "fp32",
-                   "factor_bytes": info["factor_bytes"],
-                   "l2": "inputs larger than L2: every iteration streams %.2f GB of factor tiles"
-                         % ((alg_bytes - vec_bytes) / 1e9),
-                   "parallelism": f"replicas x{world}"},
+        "dtype": DTYPE[head],
+        "data": "synthetic (seeded workloads module; %s, %s)" % (SURFACE_LABEL.get(wl.surface, wl.surface),
+                                                              RHS_LABEL.get(wl.rhs, wl.rhs)),
+        "config": _workload_config(wl, info, n, world, head_bytes, vec_bytes),
         "iterations": iters, "relres": relres,
         "setup_s": {"host_band_partition": round(host_setup_s, 3),
                     **{k: round(v, 3) for k, v in setup_s.items()},
-                    "fp32_factor_ms": round(info["setup_ms_factor"], 2)},
+                    head + "_factor_ms": round(info["setup_ms_factor"], 2)},
         "solve_schedule": schedules,
         "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
         "cpu_baseline": cpu_baseline, **extra,
@@ -392,27 +588,11 @@ def run_native(args):
     if world > 1:
         torch.distributed.destroy_process_group()
 
-
-def oracle_solve_rate(wl, sample_iterations=None):
-    """Time the CPU oracle (FP64, single-threaded SciPy SuperLU + sparse matvec)."""
-    from oracle import problems
-    t = time.time()
-    P = problems.setup_workload(wl)
-    setup = time.time() - t
-    t = time.time()
-    if sample_iterations is None:
-        res = problems.solve(P, P.f, wl.tol, wl.restart, wl.max_it)
-        dt = time.time() - t
-        return {"value": round(1.0 / dt, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                "sample": f"one full FGMRES({wl.restart}) solve to {wl.tol:g} of {wl.name} "
-                          f"({res.iterations} iterations, oracle set-up of {setup:.1f} s excluded)",
-                "iterations": res.iterations, "setup_s": round(setup, 2)}
-    raise ValueError
-
-
 def run_reference(args):
-    """The reference arm: the CPU FP64 oracle, timed on the host cores."""
-    from oracle import problems
+    """The reference arm: the CPU FP64 oracle on the host cores.  Each step is one full FGMRES
+    solve of the workload with the oracle's local solves spread over all cores (spawned
+    process pool); one single-process solve is timed once beside it."""
+    from oracle import krylov, problems
     from workloads import WORKLOADS
     world, rank, local = _dist()
     if rank != 0:
@@ -421,25 +601,36 @@ def run_reference(args):
     t = time.time()
     P = problems.setup_workload(wl)
     setup = time.time() - t
-    full = problems.solve(P, P.f, wl.tol, wl.restart, wl.max_it)    # iteration count, untimed
-    its = full.iterations
-    sample = 10
+    t = time.time()
+    one = problems.solve(P, P.f, wl.tol, wl.restart, wl.max_it)
+    one_s = time.time() - t
+    cores = _host_cores()
+    pool = OraclePool(P, cores)
     times = []
-    for i in range(args.warmup + args.steps):
-        t = time.time()
-        problems.solve(P, P.f, wl.tol, wl.restart, wl.max_it, stop_after=sample)
-        dt = time.time() - t
-        if i >= args.warmup:
-            times.append(dt * its / sample)       # scaled to one full solve
+    try:
+        for i in range(args.warmup + args.steps):
+            t = time.time()
+            res = krylov.fgmres(lambda v: P.A @ v, pool.apply, P.f, wl.tol, wl.restart, wl.max_it)
+            dt = time.time() - t
+            if i >= args.warmup:
+                times.append(dt)
+    finally:
+        pool.close()
     ms = statistics.mean(times) * 1e3
     value = 1e3 / ms
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+            "ms_p50": round(statistics.median(times) * 1e3, 1),
+            "ms_p99": round(float(np.percentile(times, 99)) * 1e3, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name},
-            "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{sample} FGMRES iterations per step scaled to the "
-                                       f"{its}-iteration solve; oracle set-up {setup:.1f} s excluded"},
+            "iterations": res.iterations, "relres": res.relres,
+            "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"one full FGMRES({wl.restart}) solve to {wl.tol:g} per step, local "
+                                       f"SuperLU solves on {cores} spawned processes; oracle set-up "
+                                       f"{setup:.1f} s excluded",
+                             "one_core": {"value": round(1.0 / one_s, 5), "cores": 1,
+                                          "sample": "one full single-process solve"}},
             "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -161,6 +161,16 @@ cpm_status ensure_band_on_device(const cpm::Band& B, int dev) {
   return CPM_OK;
 }
 
+// Which bounded device waits gave up, from the status word's diagnostic bits.
+std::string timeout_where(int h) {
+  std::string w;
+  if (h & ST_AT_LU) w += " tensor-core LU update;";
+  if (h & ST_AT_SOLVE_POLL) w += " batched solve (published value);";
+  if (h & ST_AT_SOLVE_COPY) w += " batched solve (factor copy);";
+  if (h & ST_AT_KRYLOV) w += " Arnoldi step (basis copy);";
+  return w.empty() ? std::string(" unknown") : w;
+}
+
 int sm_count(int dev) {
   int n = 0;
   cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
@@ -472,6 +482,11 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   if (hst & ST_SINGULAR) {
     cpm::set_error("oras_setup: zero pivot in a local LU factorisation");
     return CPM_ERR_SINGULAR;
+  }
+  if (hst & ST_TIMEOUT) {
+    CK(cudaMemset(pc->status, 0, sizeof(int)));
+    cpm::set_error("oras_setup: a bounded device-side wait of the factorisation gave up:" + timeout_where(hst));
+    return CPM_ERR_TIMEOUT;
   }
   if (precision == CPM_BF16) {
     cudaError_t e;
@@ -1054,7 +1069,7 @@ cpm_status oras_check_status(const oras_precond* pc, void* stream) {
   CK(cudaMemcpy(&h, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
   CK(cudaMemset(pc->status, 0, sizeof(int)));
   if (h & ST_TIMEOUT) {
-    cpm::set_error("a bounded device-side wait gave up");
+    cpm::set_error("a bounded device-side wait gave up:" + timeout_where(h));
     return CPM_ERR_TIMEOUT;
   }
   return CPM_OK;

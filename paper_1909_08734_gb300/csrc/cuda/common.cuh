@@ -13,6 +13,11 @@ constexpr int TILE_ELEMS = TILE * TILE;
 // Device status word bits (latched until oras_check_status clears them).
 constexpr int ST_TIMEOUT = 1;
 constexpr int ST_SINGULAR = 2;
+// With ST_TIMEOUT: which kernel family's bounded wait gave up (diagnostics).
+constexpr int ST_AT_LU = 16;            // tensor-core trailing update (copies / MMA completion)
+constexpr int ST_AT_SOLVE_POLL = 32;    // batched solve: a published value that never came
+constexpr int ST_AT_SOLVE_COPY = 64;    // batched solve: a factor-tile copy
+constexpr int ST_AT_KRYLOV = 128;       // Arnoldi step: a basis-batch copy
 
 // Spin limit of inter-CTA waits (each poll sleeps ~0.25-2 us): ~4 s, far above any
 // legitimate wait, then the kernel reports CPM_ERR_TIMEOUT instead of hanging.

@@ -83,6 +83,8 @@ __device__ __forceinline__ Rhs rhs_view(const GmresDev& g, int q) {
 }
 
 __device__ __forceinline__ bool stopped(const Rhs& v) { return *(volatile const int*)&v.ist[I_DONE] != 0; }
+// k, total, done, status of a right-hand side in one 16-byte load (state ints are 64-byte aligned)
+__device__ __forceinline__ int4 load_state(const Rhs& v) { return __ldcg(reinterpret_cast<const int4*>(v.ist)); }
 
 // this block's rows [r0, r0 + nr)
 __device__ __forceinline__ int block_rows(const GmresDev& g, int64_t* r0) {
@@ -180,7 +182,7 @@ __device__ __forceinline__ void stream_begin(const VStream& vs, uint64_t* bar) {
 __device__ __forceinline__ bool stream_wait(const GmresDev& g, const VStream& vs, int q) {
   const bool ok = __syncthreads_and(vs.wait(q));
   if (!ok && threadIdx.x == 0) {
-    atomicOr(g.status, ST_TIMEOUT);
+    atomicOr(g.status, ST_TIMEOUT | ST_AT_KRYLOV);
     for (int r = q; r < min(q + 2, vs.total); ++r) vs.wait(r);
   }
   return ok;
@@ -311,11 +313,12 @@ __global__ void __launch_bounds__(ST) arn_wdots_kernel(GmresDev g, const int32_t
   pdl_wait();
   const int q = blockIdx.y;
   const Rhs v = rhs_view(g, q);
-  if (stopped(v)) return;
-  const StepSmem sm = step_smem(g);
-  const int k = v.ist[I_K];
   const SL L{g.m};
-  const double s = v.st[L.sc() + S_VSCALE];
+  const int4 st4 = load_state(v);
+  const double s = __ldcg(v.st + L.sc() + S_VSCALE);
+  if (st4.z) return;
+  const StepSmem sm = step_smem(g);
+  const int k = st4.x;
   int64_t r0;
   const int nr = block_rows(g, &r0);
   const VStream vs = make_stream(g, v.V, r0, nr, k + 1, 1, sm, bar);
@@ -349,9 +352,10 @@ __global__ void __launch_bounds__(ST) arn_upd1_kernel(GmresDev g) {
   pdl_wait();
   const int q = blockIdx.y;
   const Rhs v = rhs_view(g, q);
-  if (stopped(v)) return;
+  const int4 st4 = load_state(v);
+  if (st4.z) return;
   const StepSmem sm = step_smem(g);
-  const int k = v.ist[I_K];
+  const int k = st4.x;
   const SL L{g.m};
   int64_t r0;
   const int nr = block_rows(g, &r0);
@@ -401,14 +405,34 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
   pdl_wait();
   const int q = blockIdx.y;
   const Rhs v = rhs_view(g, q);
-  if (stopped(v)) return;
+  const int4 st4 = load_state(v);
+  if (st4.z) return;
   const StepSmem sm = step_smem(g);
-  const int k = v.ist[I_K];
+  const int k = st4.x;
   const SL L{g.m};
   int64_t r0;
   const int nr = block_rows(g, &r0);
   const VStream vs = make_stream(g, v.V, r0, nr, k + 1, 1, sm, bar);
   stream_begin(vs, bar);
+  // the state the step's last block needs, loaded now (off the critical path): h1, the previous
+  // rotations, g_k, ||f||, the tolerance and the iteration counters
+  double* pre = sm.red + 1024;              // h1 [0, 128), cs [128, 256), sn [256, 384), scalars
+  int* prei = reinterpret_cast<int*>(pre + 392);
+  if (threadIdx.x >= 32 && threadIdx.x < 64) {
+    const int l = threadIdx.x - 32;
+    for (int i = l; i <= k; i += 32) pre[i] = __ldcg(v.st + L.h1() + i);
+    for (int i = l; i < k; i += 32) {
+      pre[128 + i] = __ldcg(v.st + L.cs() + i);
+      pre[256 + i] = __ldcg(v.st + L.sn() + i);
+    }
+    if (l == 0) {
+      pre[384] = __ldcg(v.st + L.g() + k);
+      pre[385] = __ldcg(v.st + L.sc() + S_NF);
+      pre[386] = __ldcg(v.st + L.sc() + S_TOL);
+      prei[0] = st4.y;                                   // total
+      prei[1] = __ldcg(v.ist + I_MAXIT);
+    }
+  }
   sum_partials(g, v.p2, k, sm);
   double acc[RU];
   double ss = 0.0;
@@ -455,24 +479,17 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
   const double tot = warp_sum(t0 + t1);
   double* st = v.st;
   int* ist = v.ist;
-  // Hessenberg column k (h1 + h2) and the previous rotations, staged in shared memory
-  double* col = sm.red;
-  double* csv = sm.red + MAX_UNITS + 8;
-  double* snv = csv + MAX_UNITS;
-  for (int i = threadIdx.x; i <= k; i += 32) col[i] = __ldcg(st + L.h1() + i) + sm.hs[i];
-  for (int i = threadIdx.x; i < k; i += 32) {
-    csv[i] = __ldcg(st + L.cs() + i);
-    snv[i] = __ldcg(st + L.sn() + i);
-  }
-  __syncwarp();
+  // Hessenberg column k = h1 + h2 and the previous rotations (prefetched at the start)
+  const double* csv = pre + 128;
+  const double* snv = pre + 256;
   if (threadIdx.x != 0) return;
   ist[I_TICKET] = 0;
   const double hn = sqrt(tot);
   // previous rotations applied down the column; the rotated entry i+1 stays in a register
-  double cur = col[0];
+  double cur = pre[0] + sm.hs[0];
   for (int i = 0; i < k; ++i) {
     const double c = csv[i], sv = snv[i];
-    const double a = cur, b = col[i + 1];
+    const double a = cur, b = pre[i + 1] + sm.hs[i + 1];
     st[L.H(i, k)] = c * a + sv * b;
     cur = -sv * a + c * b;
   }
@@ -483,16 +500,17 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
   st[L.sn() + k] = sv;
   st[L.H(k, k)] = rho;
   st[L.H(k + 1, k)] = 0.0;
-  const double gk = st[L.g() + k];
+  const double gk = pre[384];
   st[L.g() + k + 1] = -sv * gk;
   st[L.g() + k] = c * gk;
   st[L.sc() + S_HN] = hn;
   st[L.sc() + S_VSCALE] = 1.0 / hn;
-  ist[I_TOTAL] += 1;
+  const int total = prei[0] + 1;
+  ist[I_TOTAL] = total;
   ist[I_KDONE] = k + 1;
-  const double est = fabs(st[L.g() + k + 1]);
-  const double nf = st[L.sc() + S_NF], tol = st[L.sc() + S_TOL];
-  bool stop = est <= tol * nf || hn == 0.0 || k + 1 >= g.m || ist[I_TOTAL] >= ist[I_MAXIT];
+  const double est = fabs(-sv * gk);
+  const double nf = pre[385], tol = pre[386];
+  bool stop = est <= tol * nf || hn == 0.0 || k + 1 >= g.m || total >= prei[1];
   if (!isfinite(hn) || !isfinite(rho) || !isfinite(est)) {
     ist[I_STATUS] = CPM_ERR_NAN;
     stop = true;

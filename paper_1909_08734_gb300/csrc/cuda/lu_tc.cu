@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(TC_LS_THREADS) lu_update_tc_kernel(float* a, c
     issue_c(0, Jbeg);
     for (int b = 2; b < NC && b < nJ; ++b) issue_c(b, Jbeg + b);   // stage 1 holds raw A for now
     sh_ok = mbar_wait_bounded(&bar_a, 0) ? 1 : 0;
-    if (!sh_ok) atomicOr(status, ST_TIMEOUT);
+    if (!sh_ok) atomicOr(status, ST_TIMEOUT | ST_AT_LU);
     a_done = sh_ok;
   }
   __syncthreads();
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(TC_LS_THREADS) lu_update_tc_kernel(float* a, c
       const int bs = it % NB, b = it & 1;
       const uint32_t ph = (uint32_t)(it / NB) & 1;
       if (!mbar_wait_bounded(&bar_b[bs], ph)) {
-        atomicOr(status, ST_TIMEOUT);
+        atomicOr(status, ST_TIMEOUT | ST_AT_LU);
         sh_ok = 0;
       } else {
         nb_wait[bs]++;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(TC_LS_THREADS) lu_update_tc_kernel(float* a, c
       const uint32_t php = (uint32_t)(p >> 1) & 1, phc = (uint32_t)(p / NC) & 1;
       if (tid == 0 && sh_ok) {
         sh_ok = mbar_wait_bounded(&bar_mma[bp], php) ? 1 : 0;
-        if (!sh_ok) atomicOr(status, ST_TIMEOUT);
+        if (!sh_ok) atomicOr(status, ST_TIMEOUT | ST_AT_LU);
         else nm_wait[bp]++;
         // U stage p % NB is free again: stream the tile NB columns ahead into it
         if (sh_ok && p + NB < nJ) {
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(TC_LS_THREADS) lu_update_tc_kernel(float* a, c
         }
         if (sh_ok) {
           sh_ok = mbar_wait_bounded(&bar_c[cp], phc) ? 1 : 0;
-          if (!sh_ok) atomicOr(status, ST_TIMEOUT);
+          if (!sh_ok) atomicOr(status, ST_TIMEOUT | ST_AT_LU);
           else nc_wait[cp]++;
         }
       }
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(128 + 32 * EPI, 1)
     issue_c(0, Jbeg);
     for (int b = 2; b < NC && b < nJ; ++b) issue_c(b, Jbeg + b);
     sh_ok = mbar_wait_bounded(&bar_a, 0) ? 1 : 0;
-    if (!sh_ok) atomicOr(status, ST_TIMEOUT);
+    if (!sh_ok) atomicOr(status, ST_TIMEOUT | ST_AT_LU);
     a_done = sh_ok;
   }
   __syncthreads();
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(128 + 32 * EPI, 1)
     }
   }
   if (failed) {                                 // the other roles give up their waits too
-    atomicOr(status, ST_TIMEOUT);
+    atomicOr(status, ST_TIMEOUT | ST_AT_LU);
     abort_flag = 1;
   }
   // ---- drain: copies and tensor-core work still in flight complete before release ----

@@ -97,7 +97,7 @@ __device__ __forceinline__ bool poll_value(const uint64_t* p, uint32_t tag, C* v
     if ((spin & 63) == 63) {
       if (*(volatile uint32_t*)&sync[3]) return false;
       if (spin > SPIN_LIMIT) {
-        atomicOr(status, ST_TIMEOUT);
+        atomicOr(status, ST_TIMEOUT | ST_AT_SOLVE_POLL);
         atomicExch(&sync[3], 1u);
         return false;
       }
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   // is folded into the next block-wide vote
   auto stage_ready = [&](uint32_t c) -> bool {
     const bool ok = mbar_wait_bounded(&bar[c % NSTAGE], (c / NSTAGE) & 1);
-    if (!ok) { atomicOr(t.status, ST_TIMEOUT); atomicExch(&t.sync[3], 1u); }
+    if (!ok) { atomicOr(t.status, ST_TIMEOUT | ST_AT_SOLVE_COPY); atomicExch(&t.sync[3], 1u); }
     return ok;
   };
 
