@@ -23,7 +23,10 @@ Modules
 Parity status (what pins each part lives in tests/test_oracle_*.py):
   band, interp, operator, partition, RAS, FGMRES: pinned.
   ORAS local operator: pinned in its parts (argmin, conormal identity, cross points,
-  Robin scaling) and by the one-subdomain / converged-solution properties; the assembled
-  Robin rows themselves rest on a reading of Sec. 4 (R1, see local.py) and are
-  "parity unpinned" beyond those checks.
+  Robin scaling), by the one-subdomain / converged-solution properties, and as a whole
+  (tests/test_oracle_robin.py): with exact Robin data on a spherical cap the local solution
+  converges at first order under readings R1 and R3 (Table 1's order), d.q uses the normal at
+  CP_{S_j}, alpha -> infinity gives the Dirichlet transmission of Sec. 5.1, the two readings
+  differ in the boundary rows only, and a planted wrong Robin weight fails.  On a triangulated
+  surface (face normals) the Robin rows stay pinned only by the solution properties.
 """

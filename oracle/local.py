@@ -23,8 +23,9 @@ Reading R1 (default): every local unknown, including Sigma_j^{BC,A}, gets the ro
 Reading R3 (option): rows of Sigma_j^{BC,A} are (c + 6/h^2) w_i - (6/h^2) (T w)_i, i.e.
   Lap_j^h has no rows there; no boundary ghost layer is used.
 Right-hand side of every local problem: [R_j r ; 0] (Sec. 5, after Eq. localOP).
-Parity status: the ORAS row assembly rests on reading R1 and is "parity unpinned" beyond
-  the checks listed in oracle/__init__.py.
+Parity status: the assembled rows are pinned against the mathematics for analytic surfaces
+  (first-order convergence with exact Robin data under R1 and R3, the alpha -> infinity
+  Dirichlet limit, tests/test_oracle_robin.py); the choice between R1 and R3 is a reading.
 """
 from __future__ import annotations
 
