@@ -363,6 +363,16 @@ cpm_status cpm_vec_axpby(int64_t n, double a, const double* x_dev, double b, dou
  * completed, INVALID_ARG or CUDA otherwise. */
 cpm_status cpm_selftest_bounded_wait(oras_precond* pc, double limit_s, void* stream);
 
+/* Failure-detection check of the zero-pivot report; no counterpart in the paper.  Runs the
+ * set-up of oras_setup with the same arguments, but after the local matrices are assembled
+ * on the device, local column 0 of subdomain `subdomain` is set to zero in every row (as if
+ * that local matrix were singular).  The factorisation then meets a zero pivot; the call
+ * returns CPM_ERR_SINGULAR with cpm_last_error naming the lowest singular subdomain (the
+ * expected outcome), frees everything it allocated and returns no handle.  Synchronises.
+ * Errors: INVALID_ARG (as oras_setup, or subdomain out of range), OOM, CUDA. */
+cpm_status oras_setup_selftest_singular(const cpm_band* band, const cpm_part* part, double c, int transmission,
+                                        double alpha, double alpha_x, int precision, int subdomain, void* stream);
+
 /* FP64 fused multiply-add probe on the current device (the denominator of the FP64-ALU
  * roofline fractions this library reports); no counterpart in the paper.  Throughput: `blocks`
  * blocks of `threads` threads, each thread advancing `chains` (1, 2, 4 or 8) independent

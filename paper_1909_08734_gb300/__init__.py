@@ -71,6 +71,12 @@ class Band:
     def handle(self):
         return self._h
 
+    def sizes(self) -> tuple[int, int, int]:
+        """(N_A, N_G, p) without copying the band's arrays."""
+        inf = _capi.cpm_band_info()
+        _check(_capi.load().cpm_band_info_get(self._h, C.byref(inf)), "cpm_band_info_get")
+        return int(inf.n_active), int(inf.n_ghost), int(inf.p)
+
     def info(self) -> dict:
         inf = _capi.cpm_band_info()
         _check(_capi.load().cpm_band_info_get(self._h, C.byref(inf)), "cpm_band_info_get")
@@ -205,6 +211,10 @@ def cpm_partition(band: Band, n_sub: int, leaf_weights=None, n_overlap: int = 2,
 def cpm_partition_from_labels(band: Band, labels, n_overlap: int = 2, n_sub: int | None = None) -> Partition:
     """Partition from caller-supplied labels (one per active node, in [0, n_sub))."""
     lab = np.ascontiguousarray(labels, dtype=np.int32)
+    n_active = band.sizes()[0]
+    if lab.ndim != 1 or lab.size != n_active:
+        raise ValueError(f"labels must be a 1-D array of {n_active} entries (one per active node), "
+                         f"got shape {lab.shape}")
     if n_sub is None:
         n_sub = int(lab.max()) + 1 if lab.size else 0
     h_out = C.c_void_p()
@@ -273,6 +283,15 @@ def oras_setup(band: Band, part: Partition, c: float, transmission: str = "oras"
     return Preconditioner(h_out, band, part)
 
 
+def oras_setup_selftest_singular(band: Band, part: Partition, c: float, transmission: str, alpha: float,
+                                 alpha_x: float, precision: str, subdomain: int, stream=None):
+    """Set-up with local column 0 of one subdomain's matrix zeroed; returns (status, message)."""
+    st = _capi.load().oras_setup_selftest_singular(band.handle, part.handle, float(c), TRANSMISSIONS[transmission],
+                                                    float(alpha), float(alpha_x), PRECISIONS[precision],
+                                                    int(subdomain), _stream_ptr(stream))
+    return int(st), _capi.load().cpm_last_error().decode()
+
+
 def oras_plan(band: Band, part: Partition, transmission: str = "oras", precision: str = "fp64",
               restart: int = 50, nrhs: int = 1) -> dict:
     """Host-side device-memory plan of oras_setup + solves (bytes); touches no GPU."""
@@ -297,12 +316,23 @@ def cpm_op_apply_noalloc(pencil, weights, nbr, n_active: int, n_nodes: int, p: i
     """y = A x for callers that cannot allocate device memory: every argument is caller-owned
     device memory (torch CUDA tensors: pencil int32, weights float64, nbr int32, x / y
     float64); the library's scratch is a static device array, looked up on the first call
-    per device.  Calls that overlap on the GPU race on that shared array."""
+    per device.  Calls that overlap on the GPU race on that shared array.  Sizes, dtypes and
+    devices are checked here, before any launch; the index values (pencil starts, neighbours)
+    must be the band's own (cpm_band_info), as they are read without bounds checks."""
     import torch
+    P = int(p) + 1
+    dev = torch.cuda.current_device()
+    need = {"pencil": int(n_nodes) * P * P, "weights": 3 * P * int(n_nodes), "nbr": 6 * int(n_active),
+            "x": int(n_active), "y": int(n_active)}
     for t, dt, name in ((pencil, torch.int32, "pencil"), (weights, torch.float64, "weights"),
-                        (nbr, torch.int32, "nbr")):
+                        (nbr, torch.int32, "nbr"), (x, torch.float64, "x"), (y, torch.float64, "y")):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise TypeError(f"{name} must be a contiguous {dt} CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if t.numel() < need[name]:
+            raise ValueError(f"{name} has {t.numel()} entries, needs {need[name]} for n_active = {n_active}, "
+                             f"n_nodes = {n_nodes}, p = {p}")
     _check(_capi.load().cpm_op_apply_noalloc(
         C.c_void_p(pencil.data_ptr()), C.c_void_p(weights.data_ptr()), C.c_void_p(nbr.data_ptr()),
         int(n_active), int(n_nodes), int(p), float(c), float(h), _dev_ptr(x, n_active, "x"),

@@ -216,7 +216,7 @@ cpm_status set_schedule(oras_precond* pc, int ctas_per_sm, int kseg, int prefetc
 
 cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition& P, double c,
                       int transmission, double alpha, double alpha_x, int precision, bool simt_lu,
-                      cudaStream_t s) {
+                      cudaStream_t s, int zero_column_of = -1) {
   const int ns = P.n_sub;
   pc->band = &B;
   pc->n_sub = ns;
@@ -360,7 +360,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   ALLOC(ipiv, int32_t, row_off);
   ALLOC(pc->gather, int32_t, row_off);
   ALLOC(pc->scatter, int32_t, row_off);
-  ALLOC(pc->status, int, 1);
+  ALLOC(pc->status, int, 2);                  // [0] status bits, [1] lowest singular subdomain
   void* dinv;
   {
     cudaError_t e;
@@ -383,6 +383,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   CK(cudaMemcpyAsync(d_off, h_off.data(), 8 * nnz, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_val, h_val.data(), 8 * nnz, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(pc->status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(pc->status + 1, 0x7f, sizeof(int), s));
 
   cudaEvent_t e0, e1, e2;
   CK(cudaEventCreate(&e0));
@@ -392,6 +393,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   CK(cudaMemsetAsync(work, 0, wbytes * (size_t)tile_off, s));
   CK(launch_pad_identity(work, fp64, pc->d_meta, ns, t_max, s));
   CK(launch_scatter(work, fp64, d_off, d_val, nnz, s));
+  if (zero_column_of >= 0 && zero_column_of < ns) CK(launch_zero_column(work, fp64, pc->d_meta, zero_column_of, 0, s));
   CK(cudaEventRecord(e1, s));
   FactorDev f{work, pc->d_meta, ipiv, pc->status, ns, t_max, fp64 ? 1 : 0};
   int32_t *d_first, *d_last, *d_pend, *d_hiu;
@@ -477,10 +479,12 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   // chain tiles of the solves: L_{I,I-1} and U_{I,I+1} premultiplied by the diagonal inverses
   CK(launch_chain_tiles(work, fp64, pc->d_meta, ns, t_max, inv, d_tlo, d_thi, s));
   CK(cudaStreamSynchronize(s));
-  int hst = 0;
-  CK(cudaMemcpy(&hst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
+  int hst2[2] = {0, 0};
+  CK(cudaMemcpy(hst2, pc->status, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  const int hst = hst2[0];
   if (hst & ST_SINGULAR) {
-    cpm::set_error("oras_setup: zero pivot in a local LU factorisation");
+    cpm::set_error("oras_setup: zero pivot in the local LU factorisation of subdomain " +
+                   std::to_string(hst2[1]) + " (singular local matrix)");
     return CPM_ERR_SINGULAR;
   }
   if (hst & ST_TIMEOUT) {
@@ -874,6 +878,29 @@ cpm_status oras_info_get(const oras_precond* pc, oras_info* o) {
   o->tile_rows = pc->rows_total / TILE;
   o->solve_offdiag_tiles = pc->solve_offdiag_tiles;
   return CPM_OK;
+}
+
+cpm_status oras_setup_selftest_singular(const cpm_band* band, const cpm_part* part, double c, int transmission,
+                                        double alpha, double alpha_x, int precision, int subdomain, void* stream) {
+  if (!band || !part || part->p.band != &band->b || subdomain < 0 || subdomain >= part->p.n_sub || !(c > 0.0) ||
+      (precision != CPM_FP64 && precision != CPM_FP32 && precision != CPM_BF16) ||
+      (transmission != CPM_RAS && transmission != CPM_ORAS && transmission != CPM_ORAS_R3) ||
+      (transmission != CPM_RAS && !(alpha >= 0.0 && alpha_x >= 0.0))) {
+    cpm::set_error("oras_setup_selftest_singular: bad argument");
+    return CPM_ERR_INVALID_ARG;
+  }
+  oras_precond* pc = nullptr;
+  try {
+    pc = new oras_precond();
+    cpm_status st = setup_impl(pc, band->b, part->p, c, transmission, alpha, alpha_x, precision, false,
+                               (cudaStream_t)stream, subdomain);
+    delete pc;
+    return st;
+  } catch (const std::bad_alloc&) {
+    delete pc;
+    cpm::set_error("oras_setup_selftest_singular: out of host memory");
+    return CPM_ERR_OOM;
+  }
 }
 
 cpm_status oras_plan(const cpm_band* band, const cpm_part* part, int transmission, int precision,

@@ -167,17 +167,15 @@ namespace {
 // partition file: header, then N_A int32 labels
 struct PartFileHeader {
   char magic[8];              // "CPMPART1"
-  uint32_t version;           // 1
+  uint32_t version;           // 2
   int32_t n_sub, n_overlap, p;
   int64_t n_active, n_nodes;
   double h;
-  uint64_t grid_hash;         // FNV-1a over the int32 grid coordinates of every node
+  uint64_t band_hash;         // FNV-1a over the grid coordinates and closest points of every node
 };
 
-uint64_t grid_hash(const cpm::Band& B) {
-  uint64_t x = 1469598103934665603ull;
-  const unsigned char* b = (const unsigned char*)B.ijk.data();
-  const size_t n = B.ijk.size() * sizeof(int32_t);
+uint64_t fnv1a(uint64_t x, const void* data, size_t n) {
+  const unsigned char* b = (const unsigned char*)data;
   for (size_t k = 0; k < n; ++k) {
     x ^= b[k];
     x *= 1099511628211ull;
@@ -185,18 +183,25 @@ uint64_t grid_hash(const cpm::Band& B) {
   return x;
 }
 
+// The sets of Sec. 4 depend on the grid nodes and on their closest points (the generators
+// of CP_{S_j} and the cross marks), so both enter the fingerprint.
+uint64_t band_hash(const cpm::Band& B) {
+  uint64_t x = fnv1a(1469598103934665603ull, B.ijk.data(), B.ijk.size() * sizeof(B.ijk[0]));
+  return fnv1a(x, B.cp.data(), B.cp.size() * sizeof(B.cp[0]));
+}
+
 PartFileHeader header_of(const cpm::Band& B, int n_sub, int n_overlap) {
   PartFileHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "CPMPART1", 8);
-  h.version = 1;
+  h.version = 2;
   h.n_sub = n_sub;
   h.n_overlap = n_overlap;
   h.p = B.p;
   h.n_active = B.n_active;
   h.n_nodes = B.n_nodes();
   h.h = B.h;
-  h.grid_hash = grid_hash(B);
+  h.band_hash = band_hash(B);
   return h;
 }
 
@@ -237,14 +242,14 @@ cpm_status cpm_partition_load(const cpm_band* band, const char* path, cpm_part**
   }
   PartFileHeader h;
   const bool got = std::fread(&h, sizeof(h), 1, f) == 1;
-  if (!got || std::memcmp(h.magic, "CPMPART1", 8) != 0 || h.version != 1) {
+  if (!got || std::memcmp(h.magic, "CPMPART1", 8) != 0 || h.version != 2) {
     std::fclose(f);
     cpm::set_error(std::string("cpm_partition_load: not a partition file: ") + path);
     return CPM_ERR_INVALID_ARG;
   }
   const PartFileHeader mine = header_of(band->b, h.n_sub, h.n_overlap);
   if (h.p != mine.p || h.n_active != mine.n_active || h.n_nodes != mine.n_nodes || h.h != mine.h ||
-      h.grid_hash != mine.grid_hash) {
+      h.band_hash != mine.band_hash) {
     std::fclose(f);
     cpm::set_error("cpm_partition_load: the file belongs to another band");
     return CPM_ERR_INVALID_ARG;
@@ -258,9 +263,15 @@ cpm_status cpm_partition_load(const cpm_band* band, const char* path, cpm_part**
     return CPM_ERR_OOM;
   }
   const bool full = std::fread(labels.data(), sizeof(int32_t), labels.size(), f) == labels.size();
+  unsigned char extra = 0;
+  const bool trailing = full && std::fread(&extra, 1, 1, f) == 1;
   std::fclose(f);
   if (!full) {
     cpm::set_error(std::string("cpm_partition_load: truncated file: ") + path);
+    return CPM_ERR_INVALID_ARG;
+  }
+  if (trailing) {
+    cpm::set_error(std::string("cpm_partition_load: unexpected data after the labels: ") + path);
     return CPM_ERR_INVALID_ARG;
   }
   return cpm_partition_from_labels(band, h.n_sub, labels.data(), h.n_overlap, out);

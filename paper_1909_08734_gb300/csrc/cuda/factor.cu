@@ -49,6 +49,21 @@ __global__ void pad_identity_kernel(T* a, const SubMeta* __restrict__ meta) {
     at(a, m, i, i) = (T)1;
 }
 
+// Failure-detection self-test: local column col of subdomain j becomes zero in every row, as
+// if the assembled local matrix were singular (the factorisation must then report it).
+template <typename T>
+__global__ void zero_column_kernel(T* a, const SubMeta* __restrict__ meta, int j, int col) {
+  const SubMeta m = meta[j];
+  if (col < 0 || col >= m.n) return;
+  for (int i = threadIdx.x; i < 64 * m.T; i += blockDim.x) at(a, m, i, col) = (T)0;
+}
+
+cudaError_t launch_zero_column(void* a, int fp64, const SubMeta* meta, int j, int col, cudaStream_t s) {
+  if (fp64) zero_column_kernel<double><<<1, 256, 0, s>>>((double*)a, meta, j, col);
+  else zero_column_kernel<float><<<1, 256, 0, s>>>((float*)a, meta, j, col);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scatter(void* a, int fp64, const int64_t* off, const double* val, int64_t nnz,
                            cudaStream_t s) {
   if (nnz == 0) return cudaSuccess;
@@ -106,6 +121,7 @@ __global__ void __launch_bounds__(PANEL_THREADS) lu_panel_kernel(T* a, const Sub
         if (wv[w] > best || (wv[w] == best && wi[w] < bi)) { best = wv[w]; bi = wi[w]; }
       if (!(best > 0.0)) {             // zero (or NaN) column: singular local matrix
         atomicOr(status, ST_SINGULAR);
+        atomicMin(status + 1, (int)blockIdx.x);   // lowest singular subdomain
         bi = col;
       }
       piv_sh = bi;
@@ -263,7 +279,10 @@ __global__ void __launch_bounds__(PC_THREADS) lu_panel_cluster_kernel(T* a, cons
       }
       if (lane == 0) {
         if (!(v > 0.0) || loc < 0) {            // zero (or NaN) column: singular local matrix
-          if (rank == 0) atomicOr(status, ST_SINGULAR);
+          if (rank == 0) {
+            atomicOr(status, ST_SINGULAR);
+            atomicMin(status + 1, (int)(blockIdx.x / cs));   // lowest singular subdomain
+          }
           ix = -1;
         }
         piv_sh = ix;
@@ -384,6 +403,7 @@ __global__ void __launch_bounds__(ENV_THREADS) lu_envelope_kernel(int32_t* first
       const int p = ipiv[m.row_off + k0 + c] - k0;
       if (p < c || p >= nrow) {                // outside the panel's rows: cannot happen
         atomicOr(status, ST_SINGULAR);
+        atomicMin(status + 1, (int)blockIdx.x);
         continue;
       }
       const int32_t tf = F[c], tl = Lr[c];

@@ -100,6 +100,7 @@ struct FactorDev {
 };
 cudaError_t launch_scatter(void* a, int fp64, const int64_t* off, const double* val, int64_t nnz,
                            cudaStream_t s);
+cudaError_t launch_zero_column(void* a, int fp64, const SubMeta* meta, int j, int col, cudaStream_t s);
 cudaError_t launch_pad_identity(void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
                                 cudaStream_t s);
 // use_tc: 0 SIMT update, 1 tensor cores with split-tf32 operands, 2 tensor cores with bf16

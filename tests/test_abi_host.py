@@ -293,3 +293,35 @@ def test_partition_checkpoint_round_trip(tmp_path):
         with pytest.raises(G.CpmError) as e:
             G.cpm_partition_load(band, p)
         assert e.value.status == _capi.CPM_ERR_INVALID_ARG
+
+
+def test_checkpoint_fingerprint_covers_closest_points_and_size(tmp_path):
+    # two bands on the same grid nodes whose closest points differ: the sets of Sec. 4 depend
+    # on the closest points, so a partition file of one is refused by the other
+    a = G.cpm_build_band("sphere", 1.0, 0.0, 0.1, 3)
+    b = G.cpm_build_band("sphere", 1.0 + 1e-9, 0.0, 0.1, 3)
+    assert np.array_equal(a.info()["ijk"], b.info()["ijk"])
+    assert not np.array_equal(a.info()["cp"], b.info()["cp"])
+    part = G.cpm_partition(a, 4, None, 2)
+    path = tmp_path / "p.bin"
+    G.cpm_partition_save(part, str(path))
+    with pytest.raises(G.CpmError) as e:
+        G.cpm_partition_load(b, str(path))
+    assert e.value.status == _capi.CPM_ERR_INVALID_ARG and "another band" in str(e.value)
+    padded = tmp_path / "padded.bin"
+    padded.write_bytes(path.read_bytes() + b"\0\0\0\0")
+    with pytest.raises(G.CpmError) as e:
+        G.cpm_partition_load(a, str(padded))
+    assert "after the labels" in str(e.value)
+    assert np.array_equal(G.cpm_partition_load(a, str(path)).labels(), part.labels())
+
+
+def test_labels_of_the_wrong_length_are_refused_before_the_call():
+    band = G.cpm_build_band("sphere", 1.0, 0.0, 0.2, 3)
+    n = band.sizes()[0]
+    lab = (np.arange(n) % 3).astype(np.int32)
+    with pytest.raises(ValueError):
+        G.cpm_partition_from_labels(band, lab[:-1], 2, 3)
+    with pytest.raises(ValueError):
+        G.cpm_partition_from_labels(band, lab.reshape(1, -1), 2, 3)
+    assert G.cpm_partition_from_labels(band, lab, 2, 3).n_sub == 3

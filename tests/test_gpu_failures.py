@@ -5,6 +5,8 @@
   same context then solves normally.
 * A NaN in the right-hand side is reported as CPM_ERR_NAN by FGMRES and by the stationary
   solver, and the next solve on the same handle succeeds.
+* A zero pivot (one local column zeroed by the set-up self-test) is reported as
+  CPM_ERR_SINGULAR with the subdomain it belongs to.
 """
 import time
 
@@ -60,3 +62,19 @@ def test_nan_rhs_is_reported(pc):
     assert e.value.status == _capi.CPM_ERR_NAN
     res = G.cpm_gmres_solve(pc, f, u, tol=1e-8)[0]
     assert res["status"] == 0 and np.isfinite(u.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_zero_pivot_is_reported_with_its_subdomain(prec):
+    # valid inputs (c > 0) give nonsingular local matrices, so the self-test zeroes one local
+    # column of subdomain 2 between assembly and factorisation; the factorisation must report
+    # CPM_ERR_SINGULAR naming that subdomain, and the band then sets up normally
+    band = G.cpm_build_band("sphere", 1.0, 0.0, 0.2, 3)
+    part = G.cpm_partition(band, 4, None, 2)
+    st, msg = G.oras_setup_selftest_singular(band, part, 1.0, "oras", 4.0, 40.0, prec, 2)
+    assert st == _capi.CPM_ERR_SINGULAR, (st, msg)
+    assert "subdomain 2" in msg, msg
+    pc = G.oras_setup(band, part, 1.0, "oras", 4.0, 40.0, prec)
+    f = _f(pc)
+    u = torch.zeros_like(f)
+    assert G.cpm_gmres_solve(pc, f, u, tol=1e-8)[0]["status"] == 0

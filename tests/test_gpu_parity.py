@@ -45,6 +45,54 @@ def torus_uneven():
     return band, part, oras, c
 
 
+@pytest.fixture(scope="module")
+def sphere_p2():
+    # the paper's discretisation (Sec. 6): tri-quadratic interpolation, overlap 4,
+    # alpha = 4 and alpha_x = 40 (Secs. 6.5, 6.6)
+    h, c = 0.1, 1.0
+    band = G.cpm_build_band("sphere", 1.0, 0.0, h, 2)
+    part = G.cpm_partition(band, 8, None, 4)
+    oras = problems.setup("sphere", 1.0, 0.0, h, 2, c, 8, 4, "oras", 4.0, 40.0)
+    return band, part, oras, c
+
+
+def test_p2_apply_preconditioner_and_solve(sphere_p2):
+    band, part, oras, c = sphere_p2
+    assert band.info()["n_active"] == oras.band.n_active
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, "fp64")
+    n = pc.n_active
+    x = random_vector(n, 31)
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    G.cpm_op_apply(pc, _dev(x), y)
+    bound = 64 * EPS * (abs(oras.A) @ np.abs(x))
+    assert np.all(np.abs(y.cpu().numpy() - oras.A @ x) <= bound)
+    r = random_vector(n, 32)
+    z = torch.empty_like(y)
+    G.oras_apply(pc, _dev(r), z)
+    G.oras_check_status(pc)
+    ref = oras.M.apply(r)
+    assert np.linalg.norm(z.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+    cp = band.info()["cp"][:n]
+    f = (c + 12.0) * cp[:, 0] * cp[:, 1] * cp[:, 2]
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-12)[0]
+    sol = problems.solve(oras, f, 1e-12)
+    assert res["status"] == 0 and abs(res["iterations"] - sol.iterations) <= 1
+    assert np.linalg.norm(u.cpu().numpy() - sol.x) <= 1e-10 * np.linalg.norm(sol.x)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("bf16", 5e-2)])
+def test_p2_low_precision_preconditioner(sphere_p2, prec, tol):
+    band, part, oras, c = sphere_p2
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, prec)
+    r = random_vector(pc.n_active, 33)
+    z = torch.empty(pc.n_active, dtype=torch.float64, device="cuda")
+    G.oras_apply(pc, _dev(r), z)
+    G.oras_check_status(pc)
+    ref = oras.M.apply(r)
+    assert np.linalg.norm(z.cpu().numpy() - ref) <= tol * np.linalg.norm(ref)
+
+
 def test_operator_apply_parity(sphere_small):
     band, part, oras, ras, c = sphere_small
     pc = G.oras_setup(band, part, c, "ras", 0, 0, "fp64")

@@ -261,3 +261,4 @@ def test_alignment_reduces_misaligned_interface_nodes():
     lab0 = partition.rcb(B.cp[:n_a], 8)
     lab3 = partition.align_interfaces(B, lab0, 3)
     assert misaligned(lab3) < misaligned(lab0)
+
