@@ -642,7 +642,7 @@ def run_serving(args):
     capacity; p50/p99 latency (arrival to result), queue / service split; mixed (FP32
     factors) against FP64 factors."""
     import torch
-    from paper_1909_08734_gb300.serving import Request, Server, summarize
+    from paper_1909_08734_gb300.serving import Request, Server, overlap_seconds, summarize
     from workloads import (WORKLOADS, poisson_arrivals, serving_stream, smooth_rhs,
                            surface_mesh)
     V, T = surface_mesh(WORKLOADS["mesh_h001"])
@@ -652,8 +652,10 @@ def run_serving(args):
                   "0.0125} w.p. {0.5, 0.35, 0.15}, c log-uniform [0.1, 100], 1-32 rhs, 25% "
                   "backward-Euler chains, 30% operator reuse"}
 
-    def make_server(prec):
-        srv = Server(precision=prec)
+    trace = open(args.serving_trace, "a") if args.serving_trace else None
+
+    def make_server(prec, slots=1):
+        srv = Server(precision=prec, slots=slots, trace=trace)
         srv.register_surface("sphere", "sphere", 1.0, 0.0)
         srv.register_surface("torus", "torus", 1.0, 0.4)
         srv.register_surface("mesh", "trimesh", verts=V, tris=T)
@@ -670,22 +672,27 @@ def run_serving(args):
                 for sp, a in zip(specs, arrivals)]
 
     for prec in args.serving_precisions.split(","):
-        srv = make_server(prec)
-        srv._bands = host._bands                  # share host-side bands and partitions
-        cap = summarize(srv.serve(requests(np.zeros(len(specs))), realtime=False))
-        srv.close()
-        res = {"capacity": cap}
-        for frac in [float(x) for x in args.serving_load.split(",")]:
-            rate = frac * cap["requests_per_s"]
-            srv = make_server(prec)
-            srv._bands = host._bands
-            st = summarize(srv.serve(requests(poisson_arrivals(len(specs), rate, seed=5))))
-            st["offered_rate_per_s"] = rate
-            st["counters"] = dict(srv.counters)
+        res = {}
+        for slots in [int(x) for x in args.serving_slots.split(",")]:
+            srv = make_server(prec, slots)
+            srv._bands = host._bands                  # share host-side bands and partitions
+            cap = summarize(srv.serve(requests(np.zeros(len(specs))), realtime=False))
+            cap["device_overlap_s"] = round(overlap_seconds(srv.batches), 3)
             srv.close()
-            res[f"load_{frac:g}"] = st
+            row = {"capacity": cap}
+            for frac in [float(x) for x in args.serving_load.split(",")]:
+                rate = frac * cap["requests_per_s"]
+                srv = make_server(prec, slots)
+                srv._bands = host._bands
+                st = summarize(srv.serve(requests(poisson_arrivals(len(specs), rate, seed=5))))
+                st["offered_rate_per_s"] = rate
+                st["device_overlap_s"] = round(overlap_seconds(srv.batches), 3)
+                st["counters"] = dict(srv.counters)
+                srv.close()
+                row[f"load_{frac:g}"] = st
+            res[f"slots_{slots}"] = row
+            torch.cuda.empty_cache()
         out[prec] = res
-        torch.cuda.empty_cache()
     print(json.dumps(out), flush=True)
 
 
@@ -766,6 +773,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--serving-load", default="0.7", help="offered load(s), fractions of capacity")
     ap.add_argument("--serving-precisions", default="fp32,fp64")
+    ap.add_argument("--serving-trace", default="", help="file for the serving loop's per-batch trace")
+    ap.add_argument("--serving-slots", default="1,4",
+                    help="concurrent batches (own stream and host thread each); one run per value")
     ap.add_argument("--peaks", action="store_true",
                     help="FP64 FMA peak / latency probe sweep (the FP64 roofline denominator)")
     ap.add_argument("--subdomain-table", action="store_true",

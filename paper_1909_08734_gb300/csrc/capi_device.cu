@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -146,7 +147,12 @@ struct oras_precond {
 
 namespace {
 
+// Operators of one band may be set up from several host threads (serving slots); the band's
+// device copy is made once, under this lock.
+std::mutex g_band_upload_mu;
+
 cpm_status ensure_band_on_device(const cpm::Band& B, int dev) {
+  std::lock_guard<std::mutex> lock(g_band_upload_mu);
   if (B.d_device == dev) return CPM_OK;
   if (B.d_device >= 0) cpm::band_release_device(const_cast<cpm::Band&>(B));
   CK(upload(B.pencil, &B.d_pencil));
@@ -160,6 +166,12 @@ cpm_status ensure_band_on_device(const cpm::Band& B, int dev) {
   B.d_device = dev;
   return CPM_OK;
 }
+
+// Buffers initialised with cudaMemset / cudaMemcpy (the legacy default stream; a pageable
+// cudaMemcpy may return before its DMA lands) are read by kernels on the caller's stream, which
+// may be a non-blocking stream that does not wait for the legacy stream: fence the legacy
+// stream before such buffers are first used.
+cudaError_t legacy_fence() { return cudaStreamSynchronize(cudaStreamLegacy); }
 
 // Which bounded device waits gave up, from the status word's diagnostic bits.
 std::string timeout_where(int h) {
@@ -200,6 +212,7 @@ cpm_status set_schedule(oras_precond* pc, int ctas_per_sm, int kseg, int prefetc
     ALLOC(d_ptag, uint64_t, nslot);
     CK(cudaMemcpy(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
     CK(cudaMemset(d_ptag, 0, 8 * (size_t)nslot));
+    CK(legacy_fence());
     t.items = d_items;
     t.n_items = (int)items.size();
     t.ptag = d_ptag;
@@ -476,6 +489,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   ALLOC(d_thi, int32_t, n_trow);
   CK(cudaMemcpy(d_tlo, pc->tlo.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(d_thi, pc->thi.data(), 4 * (size_t)n_trow, cudaMemcpyHostToDevice));
+  CK(legacy_fence());
   // chain tiles of the solves: L_{I,I-1} and U_{I,I+1} premultiplied by the diagonal inverses
   CK(launch_chain_tiles(work, fp64, pc->d_meta, ns, t_max, inv, d_tlo, d_thi, s));
   CK(cudaStreamSynchronize(s));
@@ -488,7 +502,8 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
     return CPM_ERR_SINGULAR;
   }
   if (hst & ST_TIMEOUT) {
-    CK(cudaMemset(pc->status, 0, sizeof(int)));
+    CK(cudaMemsetAsync(pc->status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
     cpm::set_error("oras_setup: a bounded device-side wait of the factorisation gave up:" + timeout_where(hst));
     return CPM_ERR_TIMEOUT;
   }
@@ -514,6 +529,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   ALLOC(d_ytag, uint64_t, (int64_t)words * row_off);
   CK(cudaMemset(d_ytag, 0, 8 * (size_t)words * row_off));
   CK(cudaMemset(d_sync, 0, 16));
+  CK(legacy_fence());
   pc->release(dinv);
   pc->dinv = nullptr;
   TrsvDev& t = pc->trsv;
@@ -602,6 +618,7 @@ cpm_status ensure_gmres(oras_precond* pc, int m, int nr) {
   CK(cudaMemset(g.st, 0, sizeof(double) * (size_t)cap * g.st_stride));
   CK(cudaMemset(g.ist, 0, sizeof(int) * cap * GMRES_IST_STRIDE));
   CK(cudaMemset(g.ctl, 0, 4 * sizeof(int)));
+  CK(legacy_fence());
   CK(gmres_prepare(g.chunk, m));
   if (!pc->g_istate_host)
     CK(cudaMallocHost(&pc->g_istate_host, (TRSV_MAX_NR * GMRES_IST_STRIDE + 4) * sizeof(int)));
@@ -699,7 +716,8 @@ cpm_status solve_batch(oras_precond* pc, const double* f, double* u, int nr, con
     res[q].status = ih[q * GMRES_IST_STRIDE + 3];
   }
   if (dst & ST_TIMEOUT) {
-    CK(cudaMemset(pc->status, 0, sizeof(int)));
+    CK(cudaMemsetAsync(pc->status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
     for (int q = 0; q < nr; ++q) res[q].status = CPM_ERR_TIMEOUT;
   }
   return CPM_OK;
@@ -782,7 +800,8 @@ cpm_status stationary_batch(oras_precond* pc, const double* f, double* u, int nr
   int dst = 0;
   CK(cudaMemcpy(&dst, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (dst & ST_TIMEOUT) {
-    CK(cudaMemset(pc->status, 0, sizeof(int)));
+    CK(cudaMemsetAsync(pc->status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
     for (int q = 0; q < nr; ++q) res[q].status = CPM_ERR_TIMEOUT;
   }
   return CPM_OK;
@@ -1094,7 +1113,8 @@ cpm_status oras_check_status(const oras_precond* pc, void* stream) {
   CK(cudaStreamSynchronize((cudaStream_t)stream));
   int h = 0;
   CK(cudaMemcpy(&h, pc->status, sizeof(int), cudaMemcpyDeviceToHost));
-  CK(cudaMemset(pc->status, 0, sizeof(int)));
+  CK(cudaMemsetAsync(pc->status, 0, sizeof(int), (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
   if (h & ST_TIMEOUT) {
     cpm::set_error("a bounded device-side wait gave up:" + timeout_where(h));
     return CPM_ERR_TIMEOUT;

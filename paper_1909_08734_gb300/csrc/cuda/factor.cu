@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -432,11 +434,28 @@ __global__ void __launch_bounds__(ENV_THREADS) lu_envelope_kernel(int32_t* first
     }
 }
 
-// Largest cluster size the device can co-schedule with the panel kernel's shared memory.
-static int g_panel_max_cs[2] = {0, 0};
+// Largest cluster size each device can co-schedule with the panel kernel's shared memory
+// (probed once per device, under a lock: set-ups may run in several host threads, and a reader
+// must never see a half-finished probe).
+constexpr int PANEL_MAX_DEVICES = 64;
+static int g_panel_max_cs[PANEL_MAX_DEVICES][2] = {};
+static bool g_panel_probed[PANEL_MAX_DEVICES] = {};
+static std::mutex g_panel_mu;
+
+static int panel_max_cs(int fp64) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= PANEL_MAX_DEVICES) return 0;
+  std::lock_guard<std::mutex> lock(g_panel_mu);
+  return g_panel_probed[dev] ? g_panel_max_cs[dev][fp64] : 0;
+}
 
 cudaError_t lu_panel_prepare() {
-  cudaError_t e;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= PANEL_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_panel_mu);
+  if (g_panel_probed[dev]) return cudaSuccess;
   e = cudaFuncSetAttribute(lu_envelope_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(ENV_SMEM_ROWS * 2 * sizeof(int32_t)));
   if (e != cudaSuccess) return e;
@@ -449,8 +468,8 @@ cudaError_t lu_panel_prepare() {
   e = cudaFuncSetAttribute(lu_panel_cluster_kernel<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   for (int k = 0; k < 2; ++k) {
-    g_panel_max_cs[k] = 0;
-    for (int cs = 16; cs >= 1 && !g_panel_max_cs[k]; cs /= 2) {
+    int best = 0;
+    for (int cs = 16; cs >= 1 && !best; cs /= 2) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(cs);
       cfg.blockDim = dim3(PC_THREADS);
@@ -469,9 +488,11 @@ cudaError_t lu_panel_prepare() {
         cudaGetLastError();
         n = 0;
       }
-      if (n > 0) g_panel_max_cs[k] = cs;
+      if (n > 0) best = cs;
     }
+    g_panel_max_cs[dev][k] = best;
   }
+  g_panel_probed[dev] = true;
   return cudaSuccess;
 }
 
@@ -579,7 +600,7 @@ cudaError_t launch_lu_step(const FactorDev& f, int step, int use_tc, cudaStream_
   const int max_rows = env ? f.step_rows[step] : 64 * (f.t_max - step);
   int rpc = 0;
   const int cs = panel_cluster_size(max_rows, f.fp64 ? 8 : 4, &rpc);
-  const bool cluster = cs > 0 && cs <= g_panel_max_cs[f.fp64 ? 1 : 0];
+  const bool cluster = cs > 0 && cs <= panel_max_cs(f.fp64 ? 1 : 0);
   const size_t sm = 2 * 64 * 65 * (f.fp64 ? sizeof(double) : sizeof(float));
   const size_t env_smem = (size_t)std::min(max_rows, ENV_SMEM_ROWS) * 2 * sizeof(int32_t);
   auto envelope = [&]() {

@@ -669,13 +669,18 @@ static unsigned vec_blocks(int64_t n) {
 
 static size_t ysolve_smem(int m) { return sizeof(double) * (size_t)m * m; }
 
+// The dynamic shared-memory limit is an attribute of the kernel function, shared by every
+// handle in the process: it is set once to the largest size any launch may ask for (the most
+// rows per block, the longest restart), never to one handle's size, which a later handle with
+// larger blocks would exceed.
 cudaError_t gmres_prepare(int chunk, int m) {
-  const int step = (int)gmres_step_smem_bytes(chunk);
+  if (chunk > gmres_max_chunk() || m > 128) return cudaErrorInvalidValue;
+  const int step = (int)gmres_step_smem_bytes(gmres_max_chunk());
   cudaError_t e = cudaFuncSetAttribute(arn_wdots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(arn_upd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(arn_upd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(ysolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysolve_smem(m));
+    e = cudaFuncSetAttribute(ysolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ysolve_smem(128));
   return e;
 }
 

@@ -7,26 +7,35 @@ factorisation.  The server
 
 * keeps bands and partitions on the host (per surface and h) and factorised operators
   resident in HBM (per surface, h, c), least recently used first out;
-* admits work by an HBM budget: the library's device plan of an operator (oras_plan: setup
-  peak, resident factors + FGMRES workspace) plus the batch's vectors must fit after
-  evicting idle operators; a request that cannot fit even alone fails with CPM_ERR_BUDGET;
-* batches at dispatch: the oldest queued request picks the operator, and every queued
-  plain request for the same operator joins the batch; its right-hand sides go through
-  one multi-rhs cpm_gmres_solve.  Requests arriving meanwhile join the next dispatch;
+* runs up to `slots` batches at once: each slot owns a CUDA stream and a host thread, so the
+  set-up and the solves of batches on different operators overlap on the device (the library
+  releases the interpreter while it works; one operator serves one batch at a time, as a
+  handle is not thread-safe);
+* admits continuously: whenever a slot is free, the oldest queued request whose operator is
+  not busy picks the operator, and every queued plain request for the same operator joins its
+  batch (one lock-step multi-rhs cpm_gmres_solve); requests arriving meanwhile wait for the
+  next free slot, requests for a busy operator for its next batch;
+* admits by an HBM budget: a batch reserves its vectors and, for a new operator, the set-up
+  peak of the library's device plan (oras_plan); idle operators are evicted to make room,
+  operators in use never are; a batch that does not fit now waits for running batches to
+  finish, one that cannot fit even alone fails with CPM_ERR_BUDGET;
 * records per request: arrival, start of its batch, completion, status, iterations and the
-  true relative residual of every right-hand side.
+  relative residual of every right-hand side, and per batch CUDA events on its stream.
 
 Every step on the GPU runs in the library through the C ABI; this module only schedules and
 moves vectors.  Results are deterministic: a request gets bit-identical solutions whether it
-is served alone or inside a mix, because each right-hand side is solved independently with
-the operator's fixed solve schedule (the default schedule unless one is pinned per surface
-and h with `pin_schedule`).
+is served alone or inside a mix, because each right-hand side of a batch runs exactly the
+operations of a single-rhs solve with the operator's fixed solve schedule (the default
+schedule unless one is pinned per surface and h with `pin_schedule`), whatever the other
+slots do.
 """
 from __future__ import annotations
 
 import collections
+import concurrent.futures as cf
 import dataclasses
 import math
+import threading
 import time
 
 import numpy as np
@@ -53,6 +62,7 @@ class Request:
     t_done: float = math.nan
     factorised: bool = False        # this request's batch set up the operator
     batch_rhs: int = 0              # right-hand sides solved in its batch
+    slot: int = -1                  # slot that served it
 
     @property
     def nrhs(self) -> int:
@@ -66,6 +76,10 @@ class Request:
     def queue_time(self) -> float:
         return self.t_start - self.arrival
 
+    @property
+    def key(self):
+        return (self.surface, float(self.h), float(self.c))
+
 
 class _Operator:
     def __init__(self, pc, resident: int):
@@ -73,11 +87,23 @@ class _Operator:
         self.resident = resident
 
 
+@dataclasses.dataclass
+class BatchRecord:
+    """One served batch: its requests, slot, and CUDA events recorded on the slot's stream at
+    the start of its work and after its last copy (elapsed_time between two records gives the
+    device-side interval of the batch)."""
+    rids: list
+    slot: int
+    key: tuple
+    start: object
+    end: object
+
+
 class Server:
     def __init__(self, budget_bytes: int | None = None, precision: str = "fp32", restart: int = 50,
                  tol: float = 1e-8, max_it: int = 1000, method: str = "oras", alpha: float = 4.0,
                  alpha_x: float = 40.0, n_overlap: int = 2, p: int = 3, nodes_per_sub: int = 4000,
-                 keep_solutions: bool = False):
+                 keep_solutions: bool = False, slots: int = 4, trace=None):
         import torch
         self.torch = torch
         if budget_bytes is None:
@@ -95,12 +121,25 @@ class Server:
         self.p = p
         self.nodes_per_sub = nodes_per_sub
         self.keep_solutions = keep_solutions
+        self.slots = max(1, int(slots))
+        self._streams = [torch.cuda.Stream() for _ in range(self.slots)]
         self._surfaces = {}
         self._bands = {}
         self._ops: collections.OrderedDict = collections.OrderedDict()
         self._schedules = {}
-        self.used = 0
+        self._lock = threading.RLock()            # operator table, budget, counters
+        self._busy = set()                        # operator keys of batches in flight
+        self.used = 0                             # resident operators
+        self.reserved = 0                         # vectors and set-up transients in flight
         self.counters = collections.Counter()
+        self.batches: list[BatchRecord] = []
+        self.trace = trace                         # optional file: one line per batch start / end
+
+    def _log(self, msg: str):
+        if self.trace is not None:
+            with self._lock:
+                self.trace.write(msg + "\n")
+                self.trace.flush()
 
     # ---------------------------------------------------------------- registry
     def register_surface(self, name: str, kind: str, R: float = 1.0, r: float = 0.0, verts=None,
@@ -110,107 +149,155 @@ class Server:
     def band(self, surface: str, h: float):
         """(Band, Partition, closest points of the actives) of a surface at spacing h."""
         key = (surface, float(h))
-        if key not in self._bands:
-            kind, R, r, V, T = self._surfaces[surface]
-            band = cpm_build_band(kind, R, r, h, self.p, verts=V, tris=T)
-            inf = band.info()
-            n = inf["n_active"]
-            n_sub = 2 ** int(round(math.log2(max(1.0, n / self.nodes_per_sub))))
-            n_sub = int(min(512, max(2, n_sub)))
-            part = cpm_partition(band, n_sub, None, self.n_overlap)
-            self._bands[key] = (band, part, inf["cp"][:n].copy())
-        return self._bands[key]
+        with self._lock:
+            if key not in self._bands:
+                kind, R, r, V, T = self._surfaces[surface]
+                band = cpm_build_band(kind, R, r, h, self.p, verts=V, tris=T)
+                inf = band.info()
+                n = inf["n_active"]
+                n_sub = 2 ** int(round(math.log2(max(1.0, n / self.nodes_per_sub))))
+                n_sub = int(min(512, max(2, n_sub)))
+                part = cpm_partition(band, n_sub, None, self.n_overlap)
+                self._bands[key] = (band, part, inf["cp"][:n].copy())
+            return self._bands[key]
 
     def pin_schedule(self, surface: str, h: float, **knobs):
         """Solve schedule (oras_tune knobs) for every operator of this surface and h."""
         self._schedules[(surface, float(h))] = dict(knobs)
 
     # ---------------------------------------------------------------- admission
-    def _evict_one(self):
-        key, op = self._ops.popitem(last=False)
-        self.used -= op.resident
-        del op.pc
-        self.counters["evictions"] += 1
+    def _evict_idle(self, need: int) -> None:
+        """Evict least recently used operators that no batch uses until `need` more bytes fit."""
+        for key in list(self._ops.keys()):
+            if self.used + self.reserved + need <= self.budget:
+                return
+            if key in self._busy:
+                continue
+            op = self._ops.pop(key)
+            self.used -= op.resident
+            del op.pc
+            self.counters["evictions"] += 1
 
-    def _acquire(self, surface: str, h: float, c: float, vec_bytes: int):
-        """Resident operator for (surface, h, c); sets it up under the budget if needed."""
-        key = (surface, float(h), float(c))
-        if key in self._ops:
-            self._ops.move_to_end(key)
-            self.counters["operator_hits"] += 1
-            return self._ops[key].pc, False
-        band, part, _ = self.band(surface, h)
-        plan = oras_plan(band, part, self.method, self.precision, self.restart, 1)
-        need = max(plan["setup_peak_bytes"], plan["resident_bytes"]) + vec_bytes
-        if need > self.budget:
-            raise CpmError(_capi.CPM_ERR_BUDGET, f"operator {key} needs {need} bytes, budget {self.budget}")
-        while self._ops and self.used + need > self.budget:
-            self._evict_one()
-        if self.used + need > self.budget:
-            raise CpmError(_capi.CPM_ERR_BUDGET, f"operator {key} does not fit beside pinned work")
-        pc = oras_setup(band, part, c, self.method, self.alpha, self.alpha_x, self.precision)
-        for knob, value in self._schedules.get((surface, float(h)), {}).items():
+    def _reserve(self, key, nrhs: int):
+        """Reserve HBM for a batch of nrhs right-hand sides on operator `key`.  Returns
+        (reservation bytes, plan or None), or None when it does not fit now; raises
+        CPM_ERR_BUDGET when it can never fit."""
+        with self._lock:
+            band, part, cp = self.band(key[0], key[1])
+            vec_bytes = 2 * 8 * nrhs * len(cp)
+            if key in self._ops:
+                need, plan = vec_bytes, None
+            else:
+                plan = oras_plan(band, part, self.method, self.precision, self.restart, min(nrhs, 8))
+                need = max(plan["setup_peak_bytes"], plan["resident_bytes"]) + vec_bytes
+                if need > self.budget:
+                    raise CpmError(_capi.CPM_ERR_BUDGET, f"operator {key} needs {need} bytes, "
+                                                         f"budget {self.budget}")
+            self._evict_idle(need)
+            if self.used + self.reserved + need > self.budget:
+                return None
+            self.reserved += need
+            self._busy.add(key)
+            if key in self._ops:
+                self._ops.move_to_end(key)
+            return need, plan
+
+    def _operator(self, key, plan, stream):
+        """The resident operator for `key` (set up on `stream` when new); (pc, fresh)."""
+        with self._lock:
+            if key in self._ops:
+                self.counters["operator_hits"] += 1
+                return self._ops[key].pc, False
+        band, part, _ = self.band(key[0], key[1])
+        pc = oras_setup(band, part, key[2], self.method, self.alpha, self.alpha_x, self.precision,
+                        stream=stream)
+        for knob, value in self._schedules.get((key[0], key[1]), {}).items():
             oras_tune(pc, **{knob: value})
-        self._ops[key] = _Operator(pc, plan["resident_bytes"])
-        self.used += plan["resident_bytes"]
-        self.counters["setups"] += 1
+        with self._lock:
+            self._ops[key] = _Operator(pc, plan["resident_bytes"])
+            self.used += plan["resident_bytes"]
+            self.counters["setups"] += 1
         return pc, True
 
-    # ---------------------------------------------------------------- execution
-    def _solve(self, pc, F_dev, U_dev, nrhs):
-        res = cpm_gmres_solve(pc, F_dev, U_dev, nrhs=nrhs, restart=self.restart, tol=self.tol,
-                              max_it=self.max_it, raise_on_failure=False)
-        return res
+    def _release(self, key, need: int):
+        with self._lock:
+            self.reserved -= need
+            self._busy.discard(key)
 
-    def _run_batch(self, batch):
+    # ---------------------------------------------------------------- execution
+    def _solve(self, pc, F_dev, U_dev, nrhs, stream):
+        return cpm_gmres_solve(pc, F_dev, U_dev, nrhs=nrhs, restart=self.restart, tol=self.tol,
+                               max_it=self.max_it, raise_on_failure=False, stream=stream)
+
+    def _run_batch(self, batch, slot: int, plan, t0: float):
+        """One batch on one slot (its own stream): operator, copies in, the multi-rhs solve,
+        backward-Euler chains, copies out.  Runs in the slot's host thread."""
         torch = self.torch
-        head = batch[0]
-        n = len(self.band(head.surface, head.h)[2])
-        nrhs = sum(r.nrhs for r in batch)
-        vec_bytes = 2 * 8 * nrhs * n
-        try:
-            pc, fresh = self._acquire(head.surface, head.h, head.c, vec_bytes)
-        except CpmError as e:
+        stream = self._streams[slot]
+        key = batch[0].key
+        t_start = time.perf_counter() - t0
+        self._log(f"start slot={slot} key={key} rids={[r.rid for r in batch]} nrhs={sum(r.nrhs for r in batch)} "
+                  f"chains={[r.chain_steps for r in batch]} fresh={key not in self._ops}")
+        with torch.cuda.stream(stream):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            pc, fresh = self._operator(key, plan, stream)
+            nrhs = sum(r.nrhs for r in batch)
+            F = np.concatenate([r.f for r in batch], axis=0)
+            F_dev = torch.from_numpy(np.ascontiguousarray(F)).pin_memory().to("cuda", non_blocking=True)
+            U_dev = torch.empty_like(F_dev)
+            res = self._solve(pc, F_dev.view(-1), U_dev.view(-1), nrhs, stream)
+            rows, row = {}, 0
             for r in batch:
-                r.status = e.status
-            self.counters["rejected"] += len(batch)
-            return
-        for r in batch:
-            r.factorised = fresh
-            r.batch_rhs = nrhs
-        F = np.concatenate([r.f for r in batch], axis=0)
-        F_dev = torch.from_numpy(np.ascontiguousarray(F)).pin_memory().to("cuda", non_blocking=True)
-        U_dev = torch.empty_like(F_dev)
-        chains = [r for r in batch if r.chain_steps > 0]
-        res = self._solve(pc, F_dev.view(-1), U_dev.view(-1), nrhs)
-        # backward-Euler steps: f_{k+1} = u_k / dt = c u_k, same operator
-        row = 0
-        rows = {}
-        for r in batch:
-            rows[r.rid] = (row, row + r.nrhs)
-            row += r.nrhs
-        for r in chains:
-            a, b = rows[r.rid]
-            r.iterations = [x["iterations"] for x in res[a:b]]
-            r.relres = [x["relres"] for x in res[a:b]]
-            for _ in range(r.chain_steps):
-                cpm_vec_axpby(r.c, U_dev[a:b].reshape(-1), 0.0, F_dev[a:b].reshape(-1))
-                step = self._solve(pc, F_dev[a:b].reshape(-1), U_dev[a:b].reshape(-1), b - a)
-                res[a:b] = step
-                r.iterations += [x["iterations"] for x in step]
-                r.relres += [x["relres"] for x in step]
-        U = U_dev.cpu().numpy() if self.keep_solutions else None
+                rows[r.rid] = (row, row + r.nrhs)
+                row += r.nrhs
+            # backward-Euler steps: f_{k+1} = u_k / dt = c u_k, same operator
+            chains = [r for r in batch if r.chain_steps > 0]
+            for r in chains:
+                a, b = rows[r.rid]
+                r.iterations = [x["iterations"] for x in res[a:b]]
+                r.relres = [x["relres"] for x in res[a:b]]
+                for _ in range(r.chain_steps):
+                    cpm_vec_axpby(r.c, U_dev[a:b].reshape(-1), 0.0, F_dev[a:b].reshape(-1), stream=stream)
+                    step = self._solve(pc, F_dev[a:b].reshape(-1), U_dev[a:b].reshape(-1), b - a, stream)
+                    res[a:b] = step
+                    r.iterations += [x["iterations"] for x in step]
+                    r.relres += [x["relres"] for x in step]
+            U = U_dev.cpu().numpy() if self.keep_solutions else None
+            ev1.record(stream)
+            stream.synchronize()
+        t_done = time.perf_counter() - t0
+        self._log(f"done slot={slot} key={key} t={t_done - t_start:.3f}s")
         for r in batch:
             a, b = rows[r.rid]
             if r.chain_steps == 0:
                 r.iterations = [x["iterations"] for x in res[a:b]]
                 r.relres = [x["relres"] for x in res[a:b]]
             sts = [x["status"] for x in res[a:b]]
-            r.status = next((s for s in sts if s != 0), 0)
+            r.status = next((st for st in sts if st != 0), 0)
             if U is not None:
                 r.u = U[a:b].copy()
-        self.counters["batches"] += 1
-        self.counters["rhs_solved"] += nrhs + sum(r.chain_steps * r.nrhs for r in chains)
+            r.factorised = fresh
+            r.batch_rhs = nrhs
+            r.slot = slot
+            r.t_start = t_start
+            r.t_done = t_done
+        with self._lock:
+            self.batches.append(BatchRecord([r.rid for r in batch], slot, key, ev0, ev1))
+            self.counters["batches"] += 1
+            self.counters["rhs_solved"] += nrhs + sum(r.chain_steps * r.nrhs for r in chains)
+
+    def _next_batch(self, queue):
+        """The oldest queued request whose operator is idle, with the queued plain requests
+        of the same operator (a chain runs alone); None if every queued operator is busy."""
+        for head in queue:
+            if head.key in self._busy:
+                continue
+            if head.chain_steps > 0:
+                return [head]
+            return [r for r in queue if r.key == head.key and r.chain_steps == 0]
+        return None
 
     def serve(self, requests, realtime: bool = True):
         """Serve requests in arrival order (wall clock from the call); returns them, filled."""
@@ -218,36 +305,65 @@ class Server:
         pending = collections.deque(reqs)
         queue = []
         t0 = time.perf_counter()
+        free = list(range(self.slots))
+        running = {}                              # future -> (slot, key, reservation)
 
         def now():
             return time.perf_counter() - t0
 
-        while pending or queue:
-            while pending and (not realtime or pending[0].arrival <= now()):
-                queue.append(pending.popleft())
-            if not queue:
-                time.sleep(max(0.0, min(0.05, pending[0].arrival - now())))
-                continue
-            head = queue[0]
-            key = (head.surface, head.h, head.c)
-            if head.chain_steps > 0:
-                batch = [head]
-            else:
-                batch = [r for r in queue if (r.surface, r.h, r.c) == key and r.chain_steps == 0]
-            ids = {id(r) for r in batch}
-            queue = [r for r in queue if id(r) not in ids]
-            t_start = now()
-            self._run_batch(batch)
-            self.torch.cuda.synchronize()
-            t_done = now()
-            for r in batch:
-                r.t_start = t_start
-                r.t_done = t_done
+        with cf.ThreadPoolExecutor(max_workers=self.slots) as pool:
+            while pending or queue or running:
+                while pending and (not realtime or pending[0].arrival <= now()):
+                    queue.append(pending.popleft())
+                for fut in [f for f in running if f.done()]:
+                    slot, key, need = running.pop(fut)
+                    self._release(key, need)
+                    free.append(slot)
+                    fut.result()                  # a library error ends the stream here
+                dispatched = False
+                while free and queue:
+                    batch = self._next_batch(queue)
+                    if batch is None:
+                        break
+                    key = batch[0].key
+                    try:
+                        got = self._reserve(key, sum(r.nrhs for r in batch))
+                    except CpmError as e:
+                        for r in batch:
+                            r.status = e.status
+                            r.t_start = r.t_done = now()
+                        self.counters["rejected"] += len(batch)
+                        ids = {id(r) for r in batch}
+                        queue = [r for r in queue if id(r) not in ids]
+                        continue
+                    if got is None:               # waits for running batches to free HBM
+                        break
+                    need, plan = got
+                    ids = {id(r) for r in batch}
+                    queue = [r for r in queue if id(r) not in ids]
+                    slot = free.pop(0)
+                    fut = pool.submit(self._run_batch, batch, slot, plan, t0)
+                    running[fut] = (slot, key, need)
+                    dispatched = True
+                if dispatched:
+                    continue
+                if running:
+                    wait = 0.05 if not pending else max(0.0, min(0.05, pending[0].arrival - now()))
+                    cf.wait(list(running), timeout=wait, return_when=cf.FIRST_COMPLETED)
+                elif pending:
+                    time.sleep(max(0.0, min(0.05, pending[0].arrival - now())))
+                elif queue:
+                    raise RuntimeError("serving: queued work that can never be dispatched")
         return reqs
 
     def close(self):
-        while self._ops:
-            self._evict_one()
+        with self._lock:
+            self._busy.clear()
+            while self._ops:
+                key, op = self._ops.popitem(last=False)
+                self.used -= op.resident
+                del op.pc
+                self.counters["evictions"] += 1
 
 
 def summarize(reqs) -> dict:
@@ -270,4 +386,21 @@ def summarize(reqs) -> dict:
         "queue_mean_s": float(q.mean()), "service_mean_s": float(svc.mean()),
         "queue_share": float(q.sum() / lat.sum()),
         "max_relres": float(max(max(r.relres) for r in done)),
+        "slots_used": len({r.slot for r in done}),
     }
+
+
+def overlap_seconds(records) -> float:
+    """Total device time during which at least two batches of the records were in flight
+    (from their CUDA events; events of different streams are compared through elapsed_time
+    against the earliest start)."""
+    if len(records) < 2:
+        return 0.0
+    ref = records[0].start
+    iv = sorted((ref.elapsed_time(b.start) / 1e3, ref.elapsed_time(b.end) / 1e3) for b in records)
+    total, end = 0.0, iv[0][1]
+    for a, b in iv[1:]:
+        if a < end:
+            total += min(b, end) - a
+        end = max(end, b)
+    return total
