@@ -7,10 +7,11 @@ factorisation.  The server
 
 * keeps bands and partitions on the host (per surface and h) and factorised operators
   resident in HBM (per surface, h, c), least recently used first out;
-* runs up to `slots` batches at once: each slot owns a CUDA stream and a host thread, so the
-  set-up and the solves of batches on different operators overlap on the device (the library
-  releases the interpreter while it works; one operator serves one batch at a time, as a
-  handle is not thread-safe);
+* runs `slots` batches at once (default 1): each slot owns a CUDA stream and a host thread,
+  and one operator serves one batch at a time, as a handle is not thread-safe.  More than one
+  slot lets batches on different operators overlap on the device, but that mode faulted the
+  device in runs of the mixed serving stream with four slots, for a cause not yet found; it is
+  not validated and stays off unless asked for;
 * admits continuously: whenever a slot is free, the oldest queued request whose operator is
   not busy picks the operator, and every queued plain request for the same operator joins its
   batch (one lock-step multi-rhs cpm_gmres_solve); requests arriving meanwhile wait for the
@@ -103,7 +104,7 @@ class Server:
     def __init__(self, budget_bytes: int | None = None, precision: str = "fp32", restart: int = 50,
                  tol: float = 1e-8, max_it: int = 1000, method: str = "oras", alpha: float = 4.0,
                  alpha_x: float = 40.0, n_overlap: int = 2, p: int = 3, nodes_per_sub: int = 4000,
-                 keep_solutions: bool = False, slots: int = 4, trace=None):
+                 keep_solutions: bool = False, slots: int = 1, trace=None):
         import torch
         self.torch = torch
         if budget_bytes is None:
