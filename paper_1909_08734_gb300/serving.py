@@ -167,12 +167,13 @@ class Server:
         self._schedules[(surface, float(h))] = dict(knobs)
 
     # ---------------------------------------------------------------- admission
-    def _evict_idle(self, need: int) -> None:
-        """Evict least recently used operators that no batch uses until `need` more bytes fit."""
+    def _evict_idle(self, need: int, keep=None) -> None:
+        """Evict least recently used operators that no batch uses, other than `keep`, until
+        `need` more bytes fit."""
         for key in list(self._ops.keys()):
             if self.used + self.reserved + need <= self.budget:
                 return
-            if key in self._busy:
+            if key in self._busy or key == keep:
                 continue
             op = self._ops.pop(key)
             self.used -= op.resident
@@ -194,7 +195,7 @@ class Server:
                 if need > self.budget:
                     raise CpmError(_capi.CPM_ERR_BUDGET, f"operator {key} needs {need} bytes, "
                                                          f"budget {self.budget}")
-            self._evict_idle(need)
+            self._evict_idle(need, keep=key)      # the operator this batch reuses stays
             if self.used + self.reserved + need > self.budget:
                 return None
             self.reserved += need
