@@ -479,8 +479,10 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
         lo = std::min(lo, h_first[m.row_off + 64 * I + r]);
         hi = std::max(hi, h_last[m.row_off + 64 * I + r]);
       }
-      pc->tlo[tr] = lo;
-      pc->thi[tr] = std::min(hi, m.T - 1);
+      // the chain tiles L_{I,I-1} and U_{I,I+1} are always in the envelope (zero where the
+      // factors have none): each sweep is then one chain of dependencies
+      pc->tlo[tr] = I > 0 ? std::min(lo, I - 1) : lo;
+      pc->thi[tr] = I < m.T - 1 ? std::max(std::min(hi, m.T - 1), I + 1) : m.T - 1;
       pc->solve_offdiag_tiles += (I - lo) + (pc->thi[tr] - I);
     }
   }
@@ -596,10 +598,10 @@ cpm_status ensure_gmres(oras_precond* pc, int m, int nr) {
   g.nrhs = cap;
   g.status = pc->status;
   const int64_t sms = sm_count(pc->device);
+  // one block per SM (a single wave at any size): the step kernels stream a block's rows in
+  // tiles, so the rows per block are not limited by shared memory
   int64_t nblk = std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, sms));
-  int64_t chunk = ((n + nblk - 1) / nblk + 31) / 32 * 32;
-  const int64_t MAX_CHUNK = gmres_max_chunk();   // rows per block (shared memory)
-  if (chunk > MAX_CHUNK) chunk = MAX_CHUNK;
+  const int64_t chunk = ((n + nblk - 1) / nblk + 31) / 32 * 32;
   nblk = (n + chunk - 1) / chunk;
   g.nblk = (int)std::max<int64_t>(1, nblk);
   g.chunk = (int)chunk;
@@ -619,7 +621,7 @@ cpm_status ensure_gmres(oras_precond* pc, int m, int nr) {
   CK(cudaMemset(g.ist, 0, sizeof(int) * cap * GMRES_IST_STRIDE));
   CK(cudaMemset(g.ctl, 0, 4 * sizeof(int)));
   CK(legacy_fence());
-  CK(gmres_prepare(g.chunk, m));
+  CK(gmres_prepare(m));
   if (!pc->g_istate_host)
     CK(cudaMallocHost(&pc->g_istate_host, (TRSV_MAX_NR * GMRES_IST_STRIDE + 4) * sizeof(int)));
   if (!pc->g_state_host) CK(cudaMallocHost(&pc->g_state_host, TRSV_MAX_NR * 8 * sizeof(double)));

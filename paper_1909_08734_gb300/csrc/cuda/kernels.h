@@ -144,8 +144,13 @@ struct TrsvDev {
   int precision;           // 0 fp64, 1 fp32, 2 bf16
   int grid;
   int nr_cap;              // right-hand sides the tagged-word buffers hold per row
-  const int32_t* tlo;      // per tile row (row_off / 64 + I): first nonzero L tile column (or null: 0)
-  const int32_t* thi;      // per tile row: last nonzero U tile column (or null: T - 1)
+  // Tile envelope per tile row (row_off / 64 + I): L tiles [tlo, I), U tiles (I, thi].  It
+  // always holds the chain tiles L_{I,I-1} and U_{I,I+1} (zero tiles where the factors have
+  // none), so each sweep is one chain: every backward item then follows the subdomain's last
+  // forward item, and a row's backward value never overwrites its forward value (the same
+  // word) while a forward item still reads it.
+  const int32_t* tlo;      // first L tile column (or null: 0)
+  const int32_t* thi;      // last U tile column (or null: T - 1)
 };
 constexpr int TRSV_MAX_NR = 8;
 // nr in {1, 2, 4, 8} right-hand sides (r_in / z_out columns) per launch, nr <= t.nr_cap
@@ -171,7 +176,8 @@ struct GmresDev {
   double* Z;        // nrhs x (m+1) x ld: preconditioned directions (slot m: the solves of a finished rhs)
   double* w;        // nrhs x ld
   double* r;        // nrhs x ld
-  double* part;     // nrhs x part_stride: block partial sums of h1, h2 and ||w||^2
+  double* part;     // nrhs x part_stride: block partial sums of h1, h2 (vector-major: entry i of
+                    // block b at i nblk + b) and ||w||^2
   double* st;       // nrhs x st_stride: H, cs, sn, g, y, h1, scalars
   int* ist;         // nrhs x GMRES_IST_STRIDE: [0] k, [1] total, [2] done, [3] status, [4] kdone,
                     // [5] max_it, [6] slot (k, or m once the cycle stopped), [8..11] tickets
@@ -188,9 +194,8 @@ struct GmresDev {
 };
 int gmres_state_size(int m);       // doubles of state for restart length m
 int gmres_scalar_offset(int m);     // offset of the scalars (||f||, tol, beta, ||w||, relres, scale)
-size_t gmres_step_smem_bytes(int chunk);
-int gmres_max_chunk();             // most rows per block of the step kernels
-cudaError_t gmres_prepare(int chunk, int m);   // once per device and shape, before the launches
+size_t gmres_step_smem_bytes();    // dynamic shared memory of a step kernel (any rows per block)
+cudaError_t gmres_prepare(int m);  // once per device and shape, before the launches
 // begin: ||f_q|| (f_q = f + q f_stride), tolerance, iteration limit, for nr right-hand sides
 cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, int64_t f_stride, double tol, int max_it,
                                int nr, cudaStream_t s);

@@ -8,8 +8,9 @@
 //    leaves 32 lane partials per vector, which one thread then adds; a shuffle tree per value
 //    and warp would cost 5 x 32 lane additions per value;
 //  * updates w -= V_k h: one thread per row and no reduction;
-//  * block partials are added by every block of the consuming kernel in one fixed order
-//    (deterministic, no atomics); only the norm's last block finishes the step;
+//  * block partials (stored vector-major, so that one warp reads a vector's partials of all
+//    blocks in one coalesced round) are added by every block of the consuming kernel in one
+//    fixed order (deterministic, no atomics); only the norm's last block finishes the step;
 //  * v_{k+1} = w / ||w|| is no pass of its own: a step stores w unnormalised in V[k+1] with the
 //    scale 1/||w||; the next solve multiplies while it gathers (IndirectVec::scale) and the next
 //    step's first kernel normalises V[k+1] in place as it reads it.
@@ -94,45 +95,48 @@ __device__ __forceinline__ int block_rows(const GmresDev& g, int64_t* r0) {
 }
 
 // ---- staged basis stream -------------------------------------------------------------
-// A step kernel reads the basis rows of its block as a stream of batches (VB vectors x TR
-// rows); thread 0 issues the bulk copies of batch q + 2 while the block multiplies batch q, so
-// FP64 work never waits for a load.  A batch is double-buffered in shared memory with one
-// mbarrier per buffer; every wait is bounded (CPM_ERR_TIMEOUT through the status word).
+// A step kernel reads the basis rows of its block tile by tile (TR rows): for each tile one or
+// two passes over the vectors, a pass being a sequence of batches of VB vectors.  Thread 0
+// issues the bulk copies of batch q + 2 while the block multiplies batch q, so FP64 work never
+// waits for a load; a batch is double-buffered in shared memory with one mbarrier per buffer,
+// and every wait is bounded (CPM_ERR_TIMEOUT through the status word).  Only the current tile
+// of w is held in shared memory, so a block may own any number of rows and the grid is one
+// block per SM at every size.
 constexpr int VB = 8;                   // basis vectors per batch
 constexpr int TR = 1024;                // rows per tile
 constexpr int RU = TR / ST;             // rows per thread in the update pass
 constexpr int WPV = SW / VB;            // warps per vector in the dot pass
+constexpr int TJ = TR / (32 * WPV);     // 32-row groups of a tile per warp in the dot pass
 constexpr int RED_LD = 32 * WPV + 1;    // lane partials of one vector, padded
-static_assert(RU * ST == TR && WPV * VB == SW, "batch shape tied to the block shape");
+static_assert(RU * ST == TR && WPV * VB == SW && TJ % 2 == 0, "batch shape tied to the block shape");
 
 struct StepSmem {
-  double *stage, *ws, *hs, *usum, *red;
+  double *stage, *ws, *hs, *red;
 };
-// Dynamic shared memory: stage[2][VB][TR] | ws[chunk] | hs[MAX_UNITS] | usum[MAX_UNITS] |
-// red[MAX_UNITS * RED_LD]
-__device__ __forceinline__ StepSmem step_smem(const GmresDev& g) {
+// Dynamic shared memory: stage[2][VB][TR] | ws[TR] | hs[MAX_UNITS] | red[MAX_UNITS * RED_LD]
+__device__ __forceinline__ StepSmem step_smem() {
   extern __shared__ __align__(128) double dsm[];
   StepSmem s;
   s.stage = dsm;
   s.ws = dsm + 2 * VB * TR;
-  s.hs = s.ws + g.chunk;
-  s.usum = s.hs + MAX_UNITS;
-  s.red = s.usum + MAX_UNITS;
+  s.hs = s.ws + TR;
+  s.red = s.hs + MAX_UNITS;
   return s;
 }
-size_t gmres_step_smem_bytes(int chunk) {
-  return sizeof(double) * ((size_t)2 * VB * TR + (size_t)chunk + 2 * MAX_UNITS + (size_t)MAX_UNITS * RED_LD);
+size_t gmres_step_smem_bytes() {
+  return sizeof(double) * ((size_t)2 * VB * TR + TR + MAX_UNITS + (size_t)MAX_UNITS * RED_LD);
 }
-int gmres_max_chunk() { return 4032; }   // rows per block that keep a step kernel within 227 KB
 
 struct VStream {
   const double* Vb;   // the block's first row of V[0]
   int64_t ld;
   int nr, nv;         // rows of the block, vectors 0 .. nv-1
-  int ntile, nbatch, total;
+  int ntile, nbatch, npass, total;
   double* stage;
   uint64_t* bar;
-  __device__ int tile(int q) const { return (q / nbatch) % ntile; }
+  // batch q of the stream: tile-major, then pass, then batch of vectors
+  __device__ int tile(int q) const { return q / (npass * nbatch); }
+  __device__ int pass(int q) const { return (q / nbatch) % npass; }
   __device__ int batch(int q) const { return q % nbatch; }
   __device__ int rows(int q) const { return min(TR, nr - tile(q) * TR); }
   __device__ int count(int q) const { return min(VB, nv - batch(q) * VB); }
@@ -159,7 +163,8 @@ __device__ __forceinline__ VStream make_stream(const GmresDev& g, const double* 
   v.nv = nv;
   v.ntile = max(1, (nr + TR - 1) / TR);
   v.nbatch = (nv + VB - 1) / VB;
-  v.total = npass * v.ntile * v.nbatch;
+  v.npass = npass;
+  v.total = v.ntile * npass * v.nbatch;
   v.stage = sm.stage;
   v.bar = bar;
   return v;
@@ -190,8 +195,8 @@ __device__ __forceinline__ bool stream_wait(const GmresDev& g, const VStream& vs
 
 // Dot pass over batch q of the stream: warps 2s and 2s+1 own vector i0 + s and take the
 // even / odd 32-row groups of the tile; lane partials x[row] ws[row] accumulate in
-// red[i RED_LD + 32 half + lane] (started at tile 0).  scale_vec >= 0: that vector's values
-// are first multiplied by scale and written back to V.
+// red[i RED_LD + 32 half + lane] (started at the block's first tile).  scale_vec >= 0: that
+// vector's values are first multiplied by scale and written back to V.
 __device__ __forceinline__ void dots_batch(const VStream& vs, int q, const StepSmem& sm, int scale_vec,
                                            double scale, double* Vglob_row0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -201,7 +206,7 @@ __device__ __forceinline__ void dots_batch(const VStream& vs, int q, const StepS
   const int t = vs.tile(q), rows = vs.rows(q);
   const int i = vs.batch(q) * VB + slot;
   const double* x = vs.buf(q) + slot * TR;
-  const double* ws = sm.ws + t * TR;
+  const double* ws = sm.ws;
   double a0 = 0.0, a1 = 0.0;
   if (i == scale_vec) {
     double* vg = Vglob_row0 + (int64_t)i * vs.ld + (int64_t)t * TR;
@@ -212,12 +217,14 @@ __device__ __forceinline__ void dots_batch(const VStream& vs, int q, const StepS
     }
   } else if (rows == TR) {
 #pragma unroll
-    for (int j = 0; j < TR / (32 * WPV); j += 2) {
+    for (int j = 0; j < TJ; j += 2) {
       const int row = (j * WPV + half) * 32 + lane;
       a0 = fma(x[row], ws[row], a0);
       a1 = fma(x[row + 32 * WPV], ws[row + 32 * WPV], a1);
     }
   } else {
+    // a ragged tile: a loop with warp-uniform bounds (per-group predication of the unrolled
+    // loop above measured slower where this pass is the block's arithmetic bound)
     for (int row = half * 32 + lane; row < rows; row += 32 * WPV) a0 = fma(x[row], ws[row], a0);
   }
   double* r = sm.red + i * RED_LD + half * 32 + lane;
@@ -225,7 +232,7 @@ __device__ __forceinline__ void dots_batch(const VStream& vs, int q, const StepS
 }
 
 // Update pass over batch q: a[j] += sum_u x_u[row_j] hs[i0 + u] for the thread's rows
-// tid + ST j of the tile.
+// tid + ST j of the tile (vectors in increasing order).
 __device__ __forceinline__ void update_batch(const VStream& vs, int q, const StepSmem& sm, double (&a)[RU]) {
   const int cnt = vs.count(q), rows = vs.rows(q), i0 = vs.batch(q) * VB;
   const double* x = vs.buf(q);
@@ -238,26 +245,29 @@ __device__ __forceinline__ void update_batch(const VStream& vs, int q, const Ste
     }
     return;
   }
-  for (int u = 0; u < cnt; ++u) {
-    const double h = sm.hs[i0 + u];
 #pragma unroll
-    for (int j = 0; j < RU; ++j) {
-      const int row = threadIdx.x + ST * j;
-      if (row < rows) a[j] = fma(x[u * TR + row], h, a[j]);
+  for (int u = 0; u < VB; ++u) {
+    if (u < cnt) {
+      const double h = sm.hs[i0 + u];
+#pragma unroll
+      for (int j = 0; j < RU; ++j) {
+        const int row = threadIdx.x + ST * j;
+        if (row < rows) a[j] = fma(x[u * TR + row], h, a[j]);
+      }
     }
   }
 }
 
-// out[i] = sum of red[i]'s 64 lane partials for i < nv: warp w takes vectors w, w + SW, ...;
-// lane l adds its two halves, then a shuffle tree (a fixed order, no long chain of dependent
+// out[i stride] = sum of red[i]'s 64 lane partials for i < nv: warp w takes vectors w, w + SW,
+// ...; lane l adds its two halves, then a butterfly (a fixed order, no long chain of dependent
 // FP64 additions, which cost tens of cycles each on this GPU).
-__device__ __forceinline__ void finish_dots(int nv, const StepSmem& sm, double* __restrict__ out) {
+__device__ __forceinline__ void finish_dots(int nv, const StepSmem& sm, double* __restrict__ out, int stride) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = warp; i < nv; i += SW) {
     const double* p = sm.red + i * RED_LD;
     double s = p[lane] + p[lane + 32];
     s = warp_sum(s);
-    if (lane == 0) out[i] = s;
+    if (lane == 0) out[(int64_t)i * stride] = s;
   }
 }
 
@@ -275,36 +285,41 @@ __device__ __forceinline__ double block_sum(double v, double* wsum) {
   return t;
 }
 
-// hs[i] = sum over the grid's blocks of part[b (m+1) + i], i <= k; every block computes the
-// same values in the same order.  Thread (i, slice) adds the blocks slice, slice + nsl, ...
-// with two accumulators, then the nsl slices (a power of two) are added pairwise in a tree.
+// Sum of nb values p[0 .. nb) by one warp, in a fixed order (valid in every lane): lane l
+// loads p[l + 32 j] for SP_LOADS values of j at once, adds them in a tree, then a butterfly.
+constexpr int SP_LOADS = 8;             // one round covers 256 blocks
+__device__ __forceinline__ double warp_sum_blocks(const double* __restrict__ p, int nb) {
+  static_assert(SP_LOADS == 8, "the tree below adds eight loads");
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32 * SP_LOADS) {
+    double x[SP_LOADS];
+#pragma unroll
+    for (int j = 0; j < SP_LOADS; ++j) {
+      const int b = b0 + lane + 32 * j;
+      x[j] = b < nb ? __ldcg(p + b) : 0.0;
+    }
+    s += ((x[0] + x[1]) + (x[2] + x[3])) + ((x[4] + x[5]) + (x[6] + x[7]));
+  }
+  return warp_sum(s);
+}
+
+// hs[i] = sum over the grid's blocks of part[i nblk + b], i <= k; every block computes the
+// same values in the same order.  Warp w takes vectors w, w + SW, ...  (one vector at a time:
+// more in flight per warp measured slower, the registers they hold cost more than they save).
 __device__ void sum_partials(const GmresDev& g, const double* __restrict__ part, int k, const StepSmem& sm) {
   const int nv = k + 1;
-  int nsl = 1;
-  while (nsl * 2 * nv <= ST && nsl * 2 <= 64) nsl *= 2;
-  const int t = threadIdx.x;
-  const int i = t % nv, sl = t / nv;
-  if (sl < nsl) {
-    double s0 = 0.0, s1 = 0.0;
-    int b = sl;
-    for (; b + nsl < g.nblk; b += 2 * nsl) {
-      s0 += __ldcg(part + (int64_t)b * (g.m + 1) + i);
-      s1 += __ldcg(part + (int64_t)(b + nsl) * (g.m + 1) + i);
-    }
-    if (b < g.nblk) s0 += __ldcg(part + (int64_t)b * (g.m + 1) + i);
-    sm.red[sl * nv + i] = s0 + s1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < nv; i += SW) {
+    const double t = warp_sum_blocks(part + (int64_t)i * g.nblk, g.nblk);
+    if (lane == 0) sm.hs[i] = t;
   }
-  for (int h = nsl / 2; h >= 1; h /= 2) {
-    __syncthreads();
-    if (sl < h) sm.red[sl * nv + i] += sm.red[(sl + h) * nv + i];
-  }
-  __syncthreads();
-  if (t < nv) sm.hs[t] = sm.red[t];
   __syncthreads();
 }
 
-// w = A z_k on this block's rows (the operator's second half, as in nbr_sum_kernel),
-// V[k] *= s (the scale the previous step left), then partial h1 = V_k^T w.
+// w = A z_k on this block's rows (the operator's second half, as in nbr_sum_kernel), V[k] *= s
+// (the scale the previous step left), then partial h1 = V_k^T w.  The rows of w are formed tile
+// by tile, just before the tile's dot pass.
 __global__ void __launch_bounds__(ST) arn_wdots_kernel(GmresDev g, const int32_t* __restrict__ nbr,
                                                        const double* __restrict__ vext, int64_t n_nodes,
                                                        double diag, double invh2) {
@@ -317,7 +332,7 @@ __global__ void __launch_bounds__(ST) arn_wdots_kernel(GmresDev g, const int32_t
   const int4 st4 = load_state(v);
   const double s = __ldcg(v.st + L.sc() + S_VSCALE);
   if (st4.z) return;
-  const StepSmem sm = step_smem(g);
+  const StepSmem sm = step_smem();
   const int k = st4.x;
   int64_t r0;
   const int nr = block_rows(g, &r0);
@@ -325,27 +340,32 @@ __global__ void __launch_bounds__(ST) arn_wdots_kernel(GmresDev g, const int32_t
   stream_begin(vs, bar);
   const double* zk = v.Z + (int64_t)k * g.ld + r0;
   const double* ve = vext + (int64_t)q * n_nodes;
-  for (int row = threadIdx.x; row < nr; row += ST) {
-    const int32_t* nb = nbr + 6 * (r0 + row);
-    double e[6];
-#pragma unroll
-    for (int mm = 0; mm < 6; ++mm) e[mm] = __ldcg(ve + __ldg(nb + mm));
-    const double sn = ((e[0] + e[1]) + (e[2] + e[3])) + (e[4] + e[5]);
-    const double wv = diag * __ldcg(zk + row) - invh2 * sn;
-    v.w[r0 + row] = wv;
-    sm.ws[row] = wv;
-  }
   for (int qq = 0; qq < vs.total; ++qq) {
+    if (vs.batch(qq) == 0) {          // a new tile (the previous tile's dot pass has finished)
+      const int t = vs.tile(qq), rows = vs.rows(qq);
+      for (int row = threadIdx.x; row < rows; row += ST) {
+        const int64_t lr = (int64_t)t * TR + row;
+        const int32_t* nb = nbr + 6 * (r0 + lr);
+        const double e0 = __ldcg(ve + __ldg(nb + 0)), e1 = __ldcg(ve + __ldg(nb + 1));
+        const double e2 = __ldcg(ve + __ldg(nb + 2)), e3 = __ldcg(ve + __ldg(nb + 3));
+        const double e4 = __ldcg(ve + __ldg(nb + 4)), e5 = __ldcg(ve + __ldg(nb + 5));
+        const double sn = ((e0 + e1) + (e2 + e3)) + (e4 + e5);
+        const double wv = diag * __ldcg(zk + lr) - invh2 * sn;
+        v.w[r0 + lr] = wv;
+        sm.ws[row] = wv;
+      }
+    }
     if (!stream_wait(g, vs, qq)) return;
     dots_batch(vs, qq, sm, k > 0 ? k : -1, s, v.V + r0);
     __syncthreads();
     if (threadIdx.x == 0) vs.issue(qq + 2);
   }
-  finish_dots(k + 1, sm, v.p1 + (int64_t)blockIdx.x * (g.m + 1));
+  finish_dots(k + 1, sm, v.p1 + blockIdx.x, g.nblk);
 }
 
 // h1 = sum of the partials (block 0 keeps it for the Hessenberg column); w -= V_k h1; partial
-// h2 = V_k^T w.  The stream passes over the basis twice (update, then dots).
+// h2 = V_k^T w.  Per tile the stream passes over the basis twice (update, then dots; the second
+// pass reads the rows the first one has just brought into L2).
 __global__ void __launch_bounds__(ST) arn_upd1_kernel(GmresDev g) {
   __shared__ __align__(8) uint64_t bar[2];
   pdl_launch_next();
@@ -354,7 +374,7 @@ __global__ void __launch_bounds__(ST) arn_upd1_kernel(GmresDev g) {
   const Rhs v = rhs_view(g, q);
   const int4 st4 = load_state(v);
   if (st4.z) return;
-  const StepSmem sm = step_smem(g);
+  const StepSmem sm = step_smem();
   const int k = st4.x;
   const SL L{g.m};
   int64_t r0;
@@ -364,25 +384,29 @@ __global__ void __launch_bounds__(ST) arn_upd1_kernel(GmresDev g) {
   sum_partials(g, v.p1, k, sm);
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i <= k; i += ST) v.st[L.h1() + i] = sm.hs[i];
-  const int half = vs.total / 2;
-  double a[RU];
+  double a[RU], wr[RU];
   for (int qq = 0; qq < vs.total; ++qq) {
-    if (!stream_wait(g, vs, qq)) return;
-    if (qq < half) {
-      if (vs.batch(qq) == 0)
+    const int t = vs.tile(qq), rows = vs.rows(qq);
+    double* wt = v.w + r0 + (int64_t)t * TR;
+    if (vs.pass(qq) == 0 && vs.batch(qq) == 0) {   // a new tile: its rows of w, loaded early
 #pragma unroll
-        for (int j = 0; j < RU; ++j) a[j] = 0.0;
+      for (int j = 0; j < RU; ++j) {
+        const int row = threadIdx.x + ST * j;
+        a[j] = 0.0;
+        wr[j] = row < rows ? __ldcg(wt + row) : 0.0;
+      }
+    }
+    if (!stream_wait(g, vs, qq)) return;
+    if (vs.pass(qq) == 0) {
       update_batch(vs, qq, sm, a);
       if (vs.batch(qq) == vs.nbatch - 1) {
-        const int t = vs.tile(qq), rows = vs.rows(qq);
 #pragma unroll
         for (int j = 0; j < RU; ++j) {
           const int row = threadIdx.x + ST * j;
           if (row < rows) {
-            const int64_t gr = r0 + (int64_t)t * TR + row;
-            const double wn = __ldcg(v.w + gr) - a[j];
-            v.w[gr] = wn;
-            sm.ws[t * TR + row] = wn;
+            const double wn = wr[j] - a[j];
+            wt[row] = wn;
+            sm.ws[row] = wn;
           }
         }
       }
@@ -392,7 +416,7 @@ __global__ void __launch_bounds__(ST) arn_upd1_kernel(GmresDev g) {
     __syncthreads();
     if (threadIdx.x == 0) vs.issue(qq + 2);
   }
-  finish_dots(k + 1, sm, v.p2 + (int64_t)blockIdx.x * (g.m + 1));
+  finish_dots(k + 1, sm, v.p2 + blockIdx.x, g.nblk);
 }
 
 // h2 = sum of the partials; w -= V_k h2 into V[k+1] (unnormalised); ||w||^2; the last block
@@ -407,7 +431,7 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
   const Rhs v = rhs_view(g, q);
   const int4 st4 = load_state(v);
   if (st4.z) return;
-  const StepSmem sm = step_smem(g);
+  const StepSmem sm = step_smem();
   const int k = st4.x;
   const SL L{g.m};
   int64_t r0;
@@ -434,24 +458,28 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
     }
   }
   sum_partials(g, v.p2, k, sm);
-  double acc[RU];
+  double acc[RU], wr[RU];
   double ss = 0.0;
   double* vn = v.V + (int64_t)(k + 1) * g.ld + r0;
   for (int qq = 0; qq < vs.total; ++qq) {
-    if (!stream_wait(g, vs, qq)) return;
-    if (vs.batch(qq) == 0)
+    const int t = vs.tile(qq), rows = vs.rows(qq);
+    if (vs.batch(qq) == 0) {                      // a new tile: its rows of w, loaded early
 #pragma unroll
-      for (int j = 0; j < RU; ++j) acc[j] = 0.0;
+      for (int j = 0; j < RU; ++j) {
+        const int row = threadIdx.x + ST * j;
+        acc[j] = 0.0;
+        wr[j] = row < rows ? __ldcg(v.w + r0 + (int64_t)t * TR + row) : 0.0;
+      }
+    }
+    if (!stream_wait(g, vs, qq)) return;
     update_batch(vs, qq, sm, acc);
     if (vs.batch(qq) == vs.nbatch - 1) {
-      const int t = vs.tile(qq), rows = vs.rows(qq);
 #pragma unroll
       for (int j = 0; j < RU; ++j) {
         const int row = threadIdx.x + ST * j;
         if (row < rows) {
-          const int64_t lr = (int64_t)t * TR + row;
-          const double wn = __ldcg(v.w + r0 + lr) - acc[j];
-          vn[lr] = wn;
+          const double wn = wr[j] - acc[j];
+          vn[(int64_t)t * TR + row] = wn;
           ss = fma(wn, wn, ss);
         }
       }
@@ -469,33 +497,40 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
   if (!last) return;
   __threadfence();
   if (threadIdx.x >= 32) return;
-  double t0 = 0.0, t1 = 0.0;
-  int bb = threadIdx.x;
-  for (; bb + 32 < g.nblk; bb += 64) {
-    t0 += __ldcg(v.p3 + bb);
-    t1 += __ldcg(v.p3 + bb + 32);
+  const int lane = threadIdx.x;
+  const double tot = warp_sum_blocks(v.p3, g.nblk);
+  // Hessenberg column k = h1 + h2 (b) and the products of the previous rotations with it, formed
+  // by the warp so that the rotation sweep below is one dependent FMA per rotation
+  double* bcol = sm.red;                    // b_i, i <= k
+  double* cb = sm.red + 128;                // cs_i b_{i+1}
+  double* sb = sm.red + 256;                // sn_i b_{i+1}
+  for (int i = lane; i <= k; i += 32) bcol[i] = pre[i] + sm.hs[i];
+  __syncwarp();
+  for (int i = lane; i < k; i += 32) {
+    cb[i] = pre[128 + i] * bcol[i + 1];
+    sb[i] = pre[256 + i] * bcol[i + 1];
   }
-  if (bb < g.nblk) t0 += __ldcg(v.p3 + bb);
-  const double tot = warp_sum(t0 + t1);
+  __syncwarp();
+  if (lane != 0) return;
   double* st = v.st;
   int* ist = v.ist;
-  // Hessenberg column k = h1 + h2 and the previous rotations (prefetched at the start)
+  ist[I_TICKET] = 0;
   const double* csv = pre + 128;
   const double* snv = pre + 256;
-  if (threadIdx.x != 0) return;
-  ist[I_TICKET] = 0;
-  const double hn = sqrt(tot);
-  // previous rotations applied down the column; the rotated entry i+1 stays in a register
-  double cur = pre[0] + sm.hs[0];
+  // previous rotations applied down the column: H(i,k) = c_i a + s_i b_{i+1}, and the rotated
+  // entry i+1 = -s_i a + c_i b_{i+1} carries on in a register
+  double cur = bcol[0];
+#pragma unroll 4
   for (int i = 0; i < k; ++i) {
-    const double c = csv[i], sv = snv[i];
-    const double a = cur, b = pre[i + 1] + sm.hs[i + 1];
-    st[L.H(i, k)] = c * a + sv * b;
-    cur = -sv * a + c * b;
+    const double a = cur;
+    st[L.H(i, k)] = fma(csv[i], a, sb[i]);
+    cur = fma(-snv[i], a, cb[i]);
   }
-  const double a = cur, b = hn;
-  const double rho = sqrt(a * a + b * b);
-  const double c = a / rho, sv = b / rho;
+  // the new rotation zeroes ||w||: rho = sqrt(cur^2 + ||w||^2), formed from ||w||^2 directly so
+  // that it does not wait for the square root of ||w||
+  const double hn = sqrt(tot);
+  const double rho = sqrt(fma(cur, cur, tot));
+  const double c = cur / rho, sv = hn / rho;
   st[L.cs() + k] = c;
   st[L.sn() + k] = sv;
   st[L.H(k, k)] = rho;
@@ -670,12 +705,11 @@ static unsigned vec_blocks(int64_t n) {
 static size_t ysolve_smem(int m) { return sizeof(double) * (size_t)m * m; }
 
 // The dynamic shared-memory limit is an attribute of the kernel function, shared by every
-// handle in the process: it is set once to the largest size any launch may ask for (the most
-// rows per block, the longest restart), never to one handle's size, which a later handle with
-// larger blocks would exceed.
-cudaError_t gmres_prepare(int chunk, int m) {
-  if (chunk > gmres_max_chunk() || m > 128) return cudaErrorInvalidValue;
-  const int step = (int)gmres_step_smem_bytes(gmres_max_chunk());
+// handle in the process: it is set to the largest size any launch may ask for (the longest
+// restart), never to one handle's size, which a later handle would exceed.
+cudaError_t gmres_prepare(int m) {
+  if (m > 128) return cudaErrorInvalidValue;
+  const int step = (int)gmres_step_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(arn_wdots_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(arn_upd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(arn_upd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, step);
@@ -709,7 +743,7 @@ cudaError_t launch_gmres_begin(const GmresDev& g, const double* f, int64_t f_str
 
 cudaError_t launch_arnoldi_step(const GmresDev& g, const OperatorDev& op, const double* vext, int nr,
                                 cudaStream_t s) {
-  const size_t smem = gmres_step_smem_bytes(g.chunk);
+  const size_t smem = gmres_step_smem_bytes();
   const dim3 grid(g.nblk, nr);
   cudaError_t e = launch_pdl(arn_wdots_kernel, grid, smem, s, g, op.nbr, vext, op.n_nodes, op.diag, op.invh2);
   if (e == cudaSuccess) e = launch_pdl(arn_upd1_kernel, grid, smem, s, g);

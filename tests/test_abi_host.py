@@ -176,7 +176,6 @@ def test_local_order_and_tile_envelope(case):
     tracked envelope is exactly zero (the tracking rule restated from the envelope's
     definition: interchanges move (first, last) with the row; a step raises last to the pivot
     block's largest last for every row below it with first <= s)."""
-    import scipy.linalg as sla
     kind, R, r, h, p, ns, no, tr = case
     band = G.cpm_build_band(kind, R, r, h, p)
     part = G.cpm_partition(band, ns, None, no)
@@ -199,28 +198,59 @@ def test_local_order_and_tile_envelope(case):
         for s in range(T):
             below = np.nonzero(f <= s)[0]
             assert pend[s] == min(NP, max(below.max() + 1, 64 * (s + 1)))
-        # dense LU with partial pivoting of the reordered, padded matrix
-        A = np.eye(NP)
-        A[:n, :n] = 0.0
-        np.add.at(A, (pr, pc), vals)
-        lu, piv = sla.lu_factor(A, check_finite=False)
-        F, Lt = first.astype(np.int64).copy(), last.astype(np.int64).copy()
-        for s in range(T):
-            k0 = 64 * s
-            for c in range(64):
-                q = piv[k0 + c]
-                assert k0 + c <= q < pend[s]
-                F[[k0 + c, q]] = F[[q, k0 + c]]
-                Lt[[k0 + c, q]] = Lt[[q, k0 + c]]
-            hu = max(s, Lt[k0:k0 + 64].max())
-            sel = np.arange(k0 + 64, pend[s])
-            sel = sel[F[sel] <= s]
-            Lt[sel] = np.maximum(Lt[sel], hu)
+        lu, piv, tlo, thi = _tracked_envelope(n, pr, pc, vals, first, last, pend)
         for I in range(T):
-            lo, hi = F[64 * I:64 * I + 64].min(), min(T - 1, Lt[64 * I:64 * I + 64].max())
             blk = lu[64 * I:64 * I + 64]
-            assert not np.any(blk[:, :64 * lo]), (j, I, lo)
-            assert not np.any(blk[:, 64 * (hi + 1):]), (j, I, hi)
+            assert not np.any(blk[:, :64 * tlo[I]]), (j, I, tlo[I])
+            assert not np.any(blk[:, 64 * (thi[I] + 1):]), (j, I, thi[I])
+
+
+def _tracked_envelope(n, pr, pc, vals, first, last, pend):
+    """Dense LU with partial pivoting (SciPy) of the reordered, padded local matrix and the
+    tile envelope tracked with its pivots: (lu, piv, tlo, thi) with tlo / thi per tile row."""
+    import scipy.linalg as sla
+    T = (n + 63) // 64
+    NP = 64 * T
+    A = np.eye(NP)
+    A[:n, :n] = 0.0
+    np.add.at(A, (pr, pc), vals)
+    lu, piv = sla.lu_factor(A, check_finite=False)
+    F, Lt = first.astype(np.int64).copy(), last.astype(np.int64).copy()
+    for s in range(T):
+        k0 = 64 * s
+        for c in range(64):
+            q = piv[k0 + c]
+            assert k0 + c <= q < pend[s]
+            F[[k0 + c, q]] = F[[q, k0 + c]]
+            Lt[[k0 + c, q]] = Lt[[q, k0 + c]]
+        hu = max(s, Lt[k0:k0 + 64].max())
+        sel = np.arange(k0 + 64, pend[s])
+        sel = sel[F[sel] <= s]
+        Lt[sel] = np.maximum(Lt[sel], hu)
+    tlo = np.array([F[64 * I:64 * I + 64].min() for I in range(T)])
+    thi = np.array([min(T - 1, Lt[64 * I:64 * I + 64].max()) for I in range(T)])
+    return lu, piv, tlo, thi
+
+
+def test_backward_sweep_can_pass_a_forward_reader():
+    """Why the batched solve's envelope always holds the chain tiles.  In the 512-subdomain
+    torus workload (R = 1, r = 0.4, h = 0.0125, uneven leaf weights, overlap 2, ORAS),
+    subdomain 366's tile row 32 of 34 has no U tile right of its diagonal while row 33's L
+    tiles reach column 32: from the factors' envelope alone, the backward item of row 32 would
+    wait only for row 32's forward piece and could overwrite that piece's word (forward and
+    backward values of a row share it) before the forward item of row 33 has read it."""
+    from workloads import WORKLOADS, leaf_weights
+    wl = WORKLOADS["torus_h00125"]
+    band = G.cpm_build_band(wl.surface, wl.R, wl.r, wl.h, wl.p)
+    part = G.cpm_partition(band, wl.n_sub, leaf_weights(wl.n_sub, wl.weight_seed), wl.n_overlap)
+    j = 366
+    n, rows, cols, vals = G.cpm_local_coo(band, part, wl.c, wl.method, wl.alpha, wl.alpha_x, j)
+    perm, first, last, pend = G.cpm_local_order(band, part, wl.c, wl.method, wl.alpha, wl.alpha_x, j)
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    _, _, tlo, thi = _tracked_envelope(n, inv[rows], inv[cols], vals, first, last, pend)
+    T = len(tlo)
+    assert T == 34 and thi[32] == 32 and tlo[33] <= 32
 
 
 def _slab_labels(cp, n_sub):
