@@ -139,6 +139,15 @@ void cpm_band_destroy(cpm_band* band);
  * empty, align_passes outside 0..64), OOM.  Host only. */
 cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
                          int n_overlap, int align_passes, cpm_part** out);
+/* As cpm_partition, with the disjoint split by recursive graph bisection of the active
+ * 6-neighbour graph (the nearest-neighbour graph the paper partitions, Sec. 3.1) instead of
+ * coordinates: a part is ordered by breadth-first search (neighbours in neighbour-table
+ * order) from a pseudo-peripheral node, the last node reached by a search from the part's
+ * lowest index, with unreached components appended from their lowest index; the left half
+ * takes the first floor(n * W_left / W) nodes.  Same leaf weights, overlap, alignment passes,
+ * sets and errors as cpm_partition.  Host only. */
+cpm_status cpm_partition_graph(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
+                               int n_overlap, int align_passes, cpm_part** out);
 /* Labels of the N_A actives (host, int32, valid until destroy). */
 cpm_status cpm_partition_labels(const cpm_part* part, const int32_t** labels);
 /* One node set of subdomain j (CPM_SET_*), as a sorted host int32 array of global node

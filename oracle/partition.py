@@ -5,6 +5,10 @@ points of Sigma_A.  At a bisection-tree node holding n points and leaves [l0, l1
   axis = the coordinate of largest extent of the points' CP bounding box (ties: x < y < z);
   points ordered by (CP[axis], global index);
   left leaves [l0, l0 + P//2), n_left = floor(n * W_left / W) with integer leaf weights.
+Graph split (also standing in for METIS's partition of the nearest-neighbour graph,
+  Sec. 3.1): recursive bisection of the active 6-neighbour graph by the difference of the
+  graph distances to two pseudo-peripheral nodes, then size-keeping swap passes
+  (graph_bisection); the same leaf rule.
 Interface alignment (Sec. 3.2), optional passes after the split: an interface node (an
   active node with an active 6-neighbour of another label) whose nearest grid point to its
   closest point, round(CP/h) = floor(CP/h + 0.5) per axis, carries another label moves to
@@ -23,6 +27,7 @@ Cross-point nodes (Sec. 5.2.2 of the method, "Modified scheme for cross points")
 """
 from __future__ import annotations
 
+import collections
 import dataclasses
 
 import numpy as np
@@ -53,6 +58,90 @@ def rcb(points: np.ndarray, n_sub: int, leaf_weights=None) -> np.ndarray:
         nL = (len(idx) * WL) // W
         stack.append((sidx[nL:], l0 + PL, l1))
         stack.append((sidx[:nL], l0, l0 + PL))
+    return labels
+
+
+def graph_bisection(band, n_sub: int, leaf_weights=None) -> np.ndarray:
+    """Labels in [0, n_sub) for the actives by recursive bisection of the active 6-neighbour
+    graph (the nearest-neighbour graph of Sec. 3.1; reading R-graph).  Breadth-first searches
+    stay inside the part and take neighbours in neighbour-table order.  At a tree node:
+      a = the node a search from the part's lowest index reaches last, b = the node a search
+      from a reaches last; nodes sorted by (d(a, x) - d(b, x), index), nodes a does not reach
+      last by index; the first floor(n W_L / W) go left;
+      then swap passes (at most 8, until one swaps nothing): each side's nodes with a
+      neighbour across and gain = (neighbours across) - (neighbours alongside) >= 0, sorted by
+      (-gain, index); the i-th left and i-th right candidates swap when their gains at that
+      moment sum, less 2 if they are neighbours, to more than 0."""
+    na = band.n_active
+    adj = [[int(v) for v in band.nbr[g] if 0 <= v < na] for g in range(na)]
+    w = np.ones(n_sub, dtype=np.int64) if leaf_weights is None else np.asarray(leaf_weights, np.int64)
+    labels = np.full(na, -1, dtype=np.int64)
+    owner = np.zeros(na, dtype=np.int64)          # which part a node is in
+    side = np.zeros(na, dtype=np.int64)
+
+    def distances(members, part_id, start):
+        """(distance from start or -1 per node, the node reached last)."""
+        dist = {int(g): -1 for g in members}
+        dist[start] = 0
+        q = collections.deque([start])
+        last = start
+        while q:
+            u = q.popleft()
+            last = u
+            for v in adj[u]:
+                if owner[v] == part_id and dist[v] < 0:
+                    dist[v] = dist[u] + 1
+                    q.append(v)
+        return dist, last
+
+    def gain(g, part_id):
+        across = sum(1 for v in adj[g] if owner[v] == part_id and side[v] != side[g])
+        along = sum(1 for v in adj[g] if owner[v] == part_id and side[v] == side[g])
+        return across, across - along
+
+    next_id = 1
+    stack = [(np.arange(na, dtype=np.int64), 0, n_sub, 0)]
+    while stack:
+        members, l0, l1, part_id = stack.pop()
+        if l1 - l0 == 1:
+            labels[members] = l0
+            continue
+        if len(members) == 0:
+            continue
+        _, a = distances(members, part_id, int(members[0]))
+        da, b = distances(members, part_id, a)
+        db, _ = distances(members, part_id, b)
+        far = 1 << 40
+        order = sorted((int(g) for g in members),
+                       key=lambda g: (da[g] - db[g] if da[g] >= 0 else far, g))
+        PL = (l1 - l0) // 2
+        WL = int(w[l0:l0 + PL].sum())
+        W = int(w[l0:l1].sum())
+        nL = (len(members) * WL) // W
+        for q, g in enumerate(order):
+            side[g] = 0 if q < nL else 1
+        for _ in range(8):
+            left, right = [], []
+            for g in members:
+                across, gn = gain(int(g), part_id)
+                if across > 0 and gn >= 0:
+                    (left if side[g] == 0 else right).append((-gn, int(g)))
+            left.sort()
+            right.sort()
+            swaps = 0
+            for (_, u), (_, v) in zip(left, right):
+                nb = 1 if v in adj[u] else 0
+                if gain(u, part_id)[1] + gain(v, part_id)[1] - 2 * nb > 0:
+                    side[u], side[v] = 1, 0
+                    swaps += 1
+            if swaps == 0:
+                break
+        lm = members[side[members] == 0]
+        rm = members[side[members] == 1]
+        owner[lm], owner[rm] = next_id, next_id + 1
+        stack.append((rm, l0 + PL, l1, next_id + 1))
+        stack.append((lm, l0, l0 + PL, next_id))
+        next_id += 2
     return labels
 
 

@@ -194,7 +194,11 @@ def cpm_build_band(surface: str, R: float, r: float, h: float, p: int,
 
 
 def cpm_partition(band: Band, n_sub: int, leaf_weights=None, n_overlap: int = 2,
-                  align_passes: int = 0) -> Partition:
+                  align_passes: int = 0, split: str = "coordinate") -> Partition:
+    """split: "coordinate" (recursive coordinate bisection, cpm_partition) or "graph"
+    (recursive graph bisection of the active 6-neighbour graph, cpm_partition_graph)."""
+    if split not in ("coordinate", "graph"):
+        raise ValueError('split must be "coordinate" or "graph"')
     lib = _capi.load()
     wptr = None
     if leaf_weights is not None:
@@ -203,8 +207,9 @@ def cpm_partition(band: Band, n_sub: int, leaf_weights=None, n_overlap: int = 2,
             raise ValueError("leaf_weights must have n_sub entries")
         wptr = w.ctypes.data_as(C.POINTER(C.c_int64))
     h_out = C.c_void_p()
-    _check(lib.cpm_partition(band.handle, int(n_sub), wptr, int(n_overlap), int(align_passes),
-                             C.byref(h_out)), "cpm_partition")
+    fn, name = (lib.cpm_partition, "cpm_partition") if split == "coordinate" else \
+        (lib.cpm_partition_graph, "cpm_partition_graph")
+    _check(fn(band.handle, int(n_sub), wptr, int(n_overlap), int(align_passes), C.byref(h_out)), name)
     return Partition(h_out, band, n_sub)
 
 

@@ -77,6 +77,7 @@ _SIGS = {
     "cpm_band_info_get": (C.c_int, [_P, C.POINTER(cpm_band_info)]),
     "cpm_band_destroy": (None, [_P]),
     "cpm_partition": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int, C.POINTER(_P)]),
+    "cpm_partition_graph": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int, C.POINTER(_P)]),
     "cpm_partition_labels": (C.c_int, [_P, C.POINTER(C.POINTER(C.c_int32))]),
     "cpm_partition_set": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.POINTER(C.c_int32)),
                                     C.POINTER(C.c_int64)]),

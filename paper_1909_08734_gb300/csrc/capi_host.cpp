@@ -114,20 +114,20 @@ void cpm_band_destroy(cpm_band* band) {
   delete band;
 }
 
-cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
-                         int n_overlap, int align_passes, cpm_part** out) {
+static cpm_status partition_impl(const cpm_band* band, int n_sub, const int64_t* leaf_weights, int n_overlap,
+                                 int align_passes, cpm_part** out, int split, const char* name) {
   if (!band || !out) {
-    cpm::set_error("cpm_partition: NULL argument");
+    cpm::set_error(std::string(name) + ": NULL argument");
     return CPM_ERR_INVALID_ARG;
   }
   *out = nullptr;
   if (align_passes < 0 || align_passes > 64) {
-    cpm::set_error("cpm_partition: need 0 <= align_passes <= 64");
+    cpm::set_error(std::string(name) + ": need 0 <= align_passes <= 64");
     return CPM_ERR_INVALID_ARG;
   }
   try {
     cpm_part* p = new cpm_part();
-    cpm_status st = cpm::build_partition(band->b, n_sub, leaf_weights, n_overlap, align_passes, p->p);
+    cpm_status st = cpm::build_partition(band->b, n_sub, leaf_weights, n_overlap, align_passes, p->p, split);
     if (st != CPM_OK) {
       delete p;
       return st;
@@ -135,9 +135,19 @@ cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_we
     *out = p;
     return CPM_OK;
   } catch (const std::bad_alloc&) {
-    cpm::set_error("cpm_partition: out of host memory");
+    cpm::set_error(std::string(name) + ": out of host memory");
     return CPM_ERR_OOM;
   }
+}
+
+cpm_status cpm_partition(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
+                         int n_overlap, int align_passes, cpm_part** out) {
+  return partition_impl(band, n_sub, leaf_weights, n_overlap, align_passes, out, 0, "cpm_partition");
+}
+
+cpm_status cpm_partition_graph(const cpm_band* band, int n_sub, const int64_t* leaf_weights,
+                               int n_overlap, int align_passes, cpm_part** out) {
+  return partition_impl(band, n_sub, leaf_weights, n_overlap, align_passes, out, 1, "cpm_partition_graph");
 }
 
 cpm_status cpm_partition_from_labels(const cpm_band* band, int n_sub, const int32_t* labels,

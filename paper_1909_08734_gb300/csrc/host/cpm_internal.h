@@ -117,8 +117,9 @@ cpm_status build_band(const Surface& s, double h, int p, double lam_over_h, Band
 cpm_status build_band_algorithmic(const Surface& s, double h, int p, Band& out);
 // Frees the band's device copies (defined with the CUDA code).
 void band_release_device(Band& b);
+// split: 0 recursive coordinate bisection, 1 recursive graph bisection
 cpm_status build_partition(const Band& band, int n_sub, const int64_t* weights, int n_overlap,
-                           int align_passes, Partition& out);
+                           int align_passes, Partition& out, int split = 0);
 // The same sets from caller-supplied labels (every label in [0, n_sub), no subdomain empty).
 cpm_status build_partition_from_labels(const Band& band, int n_sub, const int32_t* labels, int n_overlap,
                                        Partition& out);

@@ -33,6 +33,7 @@ void rcb(const Band& B, const std::vector<int64_t>& w, std::vector<int32_t>& lab
       for (int32_t g : job.idx) labels[g] = job.l0;
       continue;
     }
+    if (job.idx.empty()) continue;     // leaves left empty: reported when the sets are built
     double mn[3], mx[3];
     for (int a = 0; a < 3; ++a) { mn[a] = mx[a] = B.cp[3 * (size_t)job.idx[0] + a]; }
     for (int32_t g : job.idx)
@@ -62,6 +63,148 @@ void rcb(const Band& B, const std::vector<int64_t>& w, std::vector<int32_t>& lab
     R.idx.assign(job.idx.begin() + nL, job.idx.end());
     L.l0 = job.l0; L.l1 = job.l0 + PL;
     R.l0 = job.l0 + PL; R.l1 = job.l1;
+    stack.push_back(std::move(R));
+    stack.push_back(std::move(L));
+  }
+}
+
+// Recursive graph bisection on the active 6-neighbour graph (standing in for the graph
+// partitioner of Sec. 3.1).  At a tree node: a = the node a breadth-first search from the
+// part's lowest index reaches last, b = the node a search from a reaches last (searches stay in
+// the part and take neighbours in neighbour-table order); the nodes are ordered by
+// (d(a, g) - d(b, g), index), nodes that a does not reach last, and the left half gets the
+// first floor(n * W_left / W) of them and leaves [l0, l0 + P/2), as in rcb; swap passes then
+// lower the cut without changing the sizes.
+void rgb(const Band& B, const std::vector<int64_t>& w, std::vector<int32_t>& labels) {
+  const int64_t na = B.n_active;
+  std::vector<int32_t> part_of(na, 0), seen(na, -1);
+  int32_t stamp = 0, next_tag = 1;
+  std::vector<int32_t> order;
+  // order := breadth-first search from root within the part (tag), then the other components
+  // (each from its lowest index); dist[g] = distance from root for the nodes the first search
+  // reaches, -1 for the others.  Returns the number of nodes the first search reached.
+  std::vector<int32_t> da(na, -1), db(na, -1);
+  auto search = [&](const std::vector<int32_t>& idx, int32_t tag, int32_t root, std::vector<int32_t>& dist) {
+    ++stamp;
+    order.clear();
+    for (int32_t g : idx) dist[g] = -1;
+    auto run = [&](int32_t s, bool first) {
+      seen[s] = stamp;
+      if (first) dist[s] = 0;
+      order.push_back(s);
+      for (size_t q = order.size() - 1; q < order.size(); ++q) {
+        const int32_t u = order[q];
+        for (int d = 0; d < 6; ++d) {
+          const int32_t v = B.nbr[6 * (size_t)u + d];
+          if (v >= 0 && v < na && part_of[v] == tag && seen[v] != stamp) {
+            seen[v] = stamp;
+            if (first) dist[v] = dist[u] + 1;
+            order.push_back(v);
+          }
+        }
+      }
+    };
+    run(root, true);
+    const size_t first = order.size();
+    for (int32_t g : idx)
+      if (seen[g] != stamp) run(g, false);
+    return first;
+  };
+  // Swap refinement of a bisection (Kernighan-Lin style, sizes kept): gain(g) = neighbours
+  // in the part on the other side - neighbours on g's side.  A pass lists each side's boundary
+  // nodes with gain >= 0 by (gain descending, index ascending) and walks the two lists in
+  // step: the i-th pair (u, v) swaps sides if, with the gains as they are at that moment,
+  // gain(u) + gain(v) - 2 [u, v neighbours] > 0.  At most 8 passes; stops at a pass without
+  // a swap.
+  std::vector<int8_t> side(na, 0);
+  auto gain = [&](int32_t g, int32_t tag, int* ext) {
+    int e = 0, i = 0;
+    for (int d = 0; d < 6; ++d) {
+      const int32_t v = B.nbr[6 * (size_t)g + d];
+      if (v >= 0 && v < na && part_of[v] == tag) (side[v] != side[g] ? e : i)++;
+    }
+    if (ext) *ext = e;
+    return e - i;
+  };
+  auto refine = [&](const std::vector<int32_t>& idx, int32_t tag) {
+    std::vector<std::pair<int, int32_t>> cl, cr;
+    for (int pass = 0; pass < 8; ++pass) {
+      cl.clear();
+      cr.clear();
+      for (int32_t g : idx) {
+        int e = 0;
+        const int gn = gain(g, tag, &e);
+        if (e > 0 && gn >= 0) (side[g] == 0 ? cl : cr).emplace_back(-gn, g);
+      }
+      std::sort(cl.begin(), cl.end());
+      std::sort(cr.begin(), cr.end());
+      int swaps = 0;
+      for (size_t q = 0; q < std::min(cl.size(), cr.size()); ++q) {
+        const int32_t u = cl[q].second, v = cr[q].second;
+        bool adj = false;
+        for (int d = 0; d < 6; ++d) adj = adj || B.nbr[6 * (size_t)u + d] == v;
+        if (gain(u, tag, nullptr) + gain(v, tag, nullptr) - 2 * (adj ? 1 : 0) > 0) {
+          side[u] = 1;
+          side[v] = 0;
+          ++swaps;
+        }
+      }
+      if (swaps == 0) break;
+    }
+  };
+  struct Job {
+    std::vector<int32_t> idx;   // ascending
+    int l0, l1;
+    int32_t tag;
+  };
+  std::vector<Job> stack;
+  std::vector<std::pair<int64_t, int32_t>> keyed;
+  Job root;
+  root.idx.resize(na);
+  std::iota(root.idx.begin(), root.idx.end(), 0);
+  root.l0 = 0;
+  root.l1 = (int)w.size();
+  root.tag = 0;
+  stack.push_back(std::move(root));
+  while (!stack.empty()) {
+    Job job = std::move(stack.back());
+    stack.pop_back();
+    const int P = job.l1 - job.l0;
+    if (P == 1) {
+      for (int32_t g : job.idx) labels[g] = job.l0;
+      continue;
+    }
+    if (job.idx.empty()) continue;     // leaves left empty: reported when the sets are built
+    // a = the last node reached from the lowest index, b = the last node reached from a;
+    // order by (d(a, g) - d(b, g), index): the cut is a level set of the difference of the two
+    // graph distances (nodes the search from a does not reach come last, by index)
+    const size_t r0 = search(job.idx, job.tag, job.idx[0], da);
+    const int32_t a = order[r0 - 1];
+    const size_t ra = search(job.idx, job.tag, a, da);
+    const int32_t b = order[ra - 1];
+    search(job.idx, job.tag, b, db);
+    keyed.clear();
+    for (int32_t g : job.idx)
+      keyed.emplace_back(da[g] >= 0 ? (int64_t)da[g] - db[g] : (int64_t)1 << 40, g);
+    std::sort(keyed.begin(), keyed.end());
+    order.clear();
+    for (auto& kg : keyed) order.push_back(kg.second);
+    const int PL = P / 2;
+    int64_t WL = 0, W = 0;
+    for (int l = job.l0; l < job.l1; ++l) {
+      W += w[l];
+      if (l < job.l0 + PL) WL += w[l];
+    }
+    const int64_t n = (int64_t)job.idx.size();
+    const int64_t nL = (n * WL) / W;
+    for (size_t q = 0; q < order.size(); ++q) side[order[q]] = (int64_t)q < nL ? 0 : 1;
+    refine(job.idx, job.tag);
+    Job L, R;
+    for (int32_t g : job.idx) (side[g] == 0 ? L.idx : R.idx).push_back(g);
+    L.l0 = job.l0; L.l1 = job.l0 + PL; L.tag = next_tag++;
+    R.l0 = job.l0 + PL; R.l1 = job.l1; R.tag = next_tag++;
+    for (int32_t g : L.idx) part_of[g] = L.tag;
+    for (int32_t g : R.idx) part_of[g] = R.tag;
     stack.push_back(std::move(R));
     stack.push_back(std::move(L));
   }
@@ -105,7 +248,7 @@ static void align_interfaces(const Band& B, int passes, std::vector<int32_t>& la
 static cpm_status finish_partition(const Band& B, Partition& part);
 
 cpm_status build_partition(const Band& B, int n_sub, const int64_t* weights, int n_overlap,
-                           int align_passes, Partition& part) {
+                           int align_passes, Partition& part, int split) {
   if (n_sub < 1 || n_overlap < 0 || n_sub > B.n_active) {
     set_error("cpm_partition: need 1 <= n_sub <= N_A and n_overlap >= 0");
     return CPM_ERR_INVALID_ARG;
@@ -125,7 +268,8 @@ cpm_status build_partition(const Band& B, int n_sub, const int64_t* weights, int
   part.n_sub = n_sub;
   part.n_overlap = n_overlap;
   part.labels.assign(na, -1);
-  rcb(B, w, part.labels);
+  if (split == 1) rgb(B, w, part.labels);
+  else rcb(B, w, part.labels);
   if (align_passes > 0) align_interfaces(B, align_passes, part.labels);
   return finish_partition(B, part);
 }
