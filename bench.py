@@ -715,8 +715,8 @@ def run_subdomain_table(args):
     out = {"mode": "subdomain_table", "surface": "unit sphere", "h": h, "p": p, "N_A": n, "overlap": 4,
            "tol": 1e-6, "factors": args.precision, "rows": []}
     for ns in [int(x) for x in args.table_subdomains.split(",")]:
-        part = G.cpm_partition(band, ns, None, 4, align_passes=args.table_align)
-        row = {"n_sub": ns, "align_passes": args.table_align, "paper_ras_solver_ras_prec_oras_solver_oras_prec":
+        part = G.cpm_partition(band, ns, None, 4, align_passes=args.table_align, split=args.table_split)
+        row = {"n_sub": ns, "align_passes": args.table_align, "split": args.table_split, "paper_ras_solver_ras_prec_oras_solver_oras_prec":
                [PAPER_SUBDOMAIN_TABLE.get(ns, (None,) * 4)[i] for i in (0, 2, 1, 3)]}
         for method in ("ras", "oras"):
             t0 = time.time()
@@ -782,6 +782,8 @@ def main():
     ap.add_argument("--subdomain-table", action="store_true",
                     help="iteration counts against the paper's subdomain-count table")
     ap.add_argument("--table-subdomains", default="32,64,96")
+    ap.add_argument("--table-split", default="coordinate", choices=["coordinate", "graph"],
+                    help="disjoint split of the subdomain table: coordinate or graph bisection")
     ap.add_argument("--table-align", type=int, default=3,
                     help="interface alignment passes (the paper uses p + 1 = 3)")
     args = ap.parse_args()

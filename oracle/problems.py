@@ -29,12 +29,14 @@ class OracleProblem:
 def setup(surface_kind: str, R: float, r: float, h: float, p: int, c: float, n_sub: int,
           n_overlap: int, method: str, alpha: float = 4.0, alpha_x: float = 40.0,
           leaf_weights=None, lam_over_h=None, reading: str = "R1",
-          dense: bool = False, verts=None, tris=None, align_passes: int = 0) -> OracleProblem:
+          dense: bool = False, verts=None, tris=None, align_passes: int = 0,
+          split: str = "coordinate") -> OracleProblem:
     surf = geometry.make_surface(surface_kind, R, r, verts, tris)
     B = band_mod.build_band(surf, h, p, lam_over_h)
     E = interp.extension_matrix(B)
     A = operator.cpm_matrix(B, E, c)
-    labels = partition.rcb(B.cp[:B.n_active], n_sub, leaf_weights)
+    labels = partition.rcb(B.cp[:B.n_active], n_sub, leaf_weights) if split == "coordinate" else \
+        partition.graph_bisection(B, n_sub, leaf_weights)
     if align_passes:
         labels = partition.align_interfaces(B, labels, align_passes)
     robin = method == "oras" and reading == "R1"

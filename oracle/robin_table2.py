@@ -27,16 +27,18 @@ PAPER_SOLVER = [19, 14, 11, 11, 15, 20, 33, 49, 67, 83]
 PAPER_PRECOND = [11, 9, 9, 8, 8, 9, 11, 13, 15, 17]
 
 
-def run(h: float, alphas, readings, tol: float = 1e-6, c: float = 1.0, align_passes: int = 0):
+def run(h: float, alphas, readings, tol: float = 1e-6, c: float = 1.0, align_passes: int = 0,
+        split: str = "coordinate"):
     rows = []
     for a in alphas:
         for rd in (readings if math.isfinite(a) else ["-"]):
             t0 = time.time()
             if math.isfinite(a):
                 P = problems.setup("sphere", 1.0, 0.0, h, 2, c, 2, 4, "oras", a, a, reading=rd,
-                                   align_passes=align_passes)
+                                   align_passes=align_passes, split=split)
             else:
-                P = problems.setup("sphere", 1.0, 0.0, h, 2, c, 2, 4, "ras", align_passes=align_passes)
+                P = problems.setup("sphere", 1.0, 0.0, h, 2, c, 2, 4, "ras", align_passes=align_passes,
+                                   split=split)
             cp = P.band.cp[:P.band.n_active]
             f = (c + 12.0) * cp[:, 0] * cp[:, 1] * cp[:, 2]
             _, it_s, ok_s = schwarz.stationary_solve(P.A, P.M, f, tol, 2000)
@@ -51,12 +53,14 @@ def main():
     ap.add_argument("--alphas", default=",".join(str(a) for a in PAPER_ALPHAS))
     ap.add_argument("--readings", default="R1,R3")
     ap.add_argument("--align", type=int, default=0, help="interface alignment passes (Sec. 3.2)")
+    ap.add_argument("--split", default="coordinate", choices=["coordinate", "graph"],
+                    help="disjoint split: coordinate or graph bisection")
     args = ap.parse_args()
     alphas = [float(x) for x in args.alphas.split(",")]
-    rows = run(args.h, alphas, args.readings.split(","), align_passes=args.align)
+    rows = run(args.h, alphas, args.readings.split(","), align_passes=args.align, split=args.split)
     paper = dict(zip(PAPER_ALPHAS, zip(PAPER_SOLVER, PAPER_PRECOND)))
-    print(f"unit sphere, p = 2, h = {args.h:g}, 2 subdomains, N_O = 4, {args.align} alignment "
-          "passes, 1e6 reduction\n")
+    print(f"unit sphere, p = 2, h = {args.h:g}, 2 subdomains ({args.split} bisection), N_O = 4, "
+          f"{args.align} alignment passes, 1e6 reduction\n")
     print("| alpha | reading | solver (paper) | solver (oracle) | preconditioner (paper) | "
           "preconditioner (oracle, right-preconditioned FGMRES) | set-up + solves s |")
     print("|---|---|---|---|---|---|---|")

@@ -309,3 +309,32 @@ def test_algorithmic_band_preconditioner_and_solve():
     gref = krylov.fgmres(lambda x: A @ x, M.apply, f, 1e-12)
     assert res["status"] == 0 and abs(res["iterations"] - gref.iterations) <= 1
     assert np.linalg.norm(u.cpu().numpy() - gref.x) / np.linalg.norm(gref.x) <= 1e-10
+
+
+@pytest.mark.gpu
+def test_graph_partition_preconditioner_and_solve():
+    """The graph bisection's subdomains (connected parts with irregular interfaces and more
+    cross points than the coordinate cuts): M^{-1} r against the oracle built from the same
+    labels (FP64 1e-10, FP32 1e-3) and the FGMRES solution."""
+    h, c = 0.1, 1.0
+    band = G.cpm_build_band("sphere", 1.0, 0.0, h, 3)
+    part = G.cpm_partition(band, 8, None, 2, split="graph")
+    P = problems.setup("sphere", 1.0, 0.0, h, 3, c, 8, 2, "oras", 4.0, 40.0, split="graph")
+    assert np.array_equal(part.labels(), P.labels)
+    r = random_vector(band.sizes()[0], 9)
+    ref = P.M.apply(r)
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-3)):
+        pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, prec)
+        z = torch.empty(pc.n_active, dtype=torch.float64, device="cuda")
+        G.oras_apply(pc, _dev(r), z)
+        G.oras_check_status(pc)
+        err = np.linalg.norm(z.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= tol, (prec, err)
+    pc = G.oras_setup(band, part, c, "oras", 4.0, 40.0, "fp64")
+    cp = band.info()["cp"][: pc.n_active]
+    f = (c + 12.0) * cp[:, 0] * cp[:, 1] * cp[:, 2]
+    u = torch.zeros(pc.n_active, dtype=torch.float64, device="cuda")
+    res = G.cpm_gmres_solve(pc, _dev(f), u, tol=1e-12)[0]
+    x = problems.solve(P, f, 1e-12).x
+    assert res["status"] == 0
+    assert np.linalg.norm(u.cpu().numpy() - x) <= 1e-10 * np.linalg.norm(x)
