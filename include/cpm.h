@@ -18,7 +18,8 @@
  *    dimension).  The library never frees them.  Host arrays returned by *_info / getters
  *    stay valid until the owning handle is destroyed.
  *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default stream).
- *  - Setup calls (cpm_build_band, cpm_partition) are host-only and never touch a GPU.
+ *  - Setup calls (cpm_build_band, cpm_partition) are host-only and never touch a GPU
+ *    (cpm_build_band_device is the device variant of cpm_build_band).
  *    oras_setup synchronises its stream before returning.  cpm_op_apply and oras_apply
  *    are asynchronous on the stream.  cpm_gmres_solve synchronises once per restart cycle.
  */
@@ -111,6 +112,17 @@ typedef struct {
  * some node leaves the active set: lambda too small), OOM.  Host only. */
 cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
                           cpm_band** out);
+/* The band of cpm_build_band, built on the current CUDA device (no counterpart in the paper,
+ * whose global meshing is serial, Sec. 6.6): closest points and the tube test of every grid node
+ * of the bounding box, order-preserving compactions for the canonical order and the ghosts, the
+ * neighbour table, stencil bases, 1-D weights and z-pencil starts, each a device kernel.  The
+ * result equals cpm_build_band's bit for bit (the device arithmetic follows the host's
+ * operations in the same order, without contraction); the host arrays are filled from the
+ * device, and the device copies the operators use stay resident (oras_setup on the same device
+ * does not upload them again).  stream: cudaStream_t as void* (NULL = legacy default stream);
+ * the call synchronises it.  Errors: as cpm_build_band, and CUDA / OOM from the device. */
+cpm_status cpm_build_band_device(const cpm_surface* surface, double h, int p, double lambda_over_h,
+                                 void* stream, cpm_band** out);
 /* Algorithmic band (Sec. 2.1: the active nodes are all nodes used for interpolation; the
  * paper takes this construction for triangulated surfaces and cites its algorithm).
  * Reading: Sigma_A is the smallest node set that contains the grid nodes within h of the

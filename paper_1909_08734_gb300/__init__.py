@@ -168,9 +168,11 @@ class Preconditioner:
 # ---------------------------------------------------------------- entry points
 def cpm_build_band(surface: str, R: float, r: float, h: float, p: int,
                    lambda_over_h: float = 0.0, verts=None, tris=None,
-                   construction: str = "tube") -> Band:
+                   construction: str = "tube", on_device: bool = False, stream=None) -> Band:
     """Band of a sphere / torus (R, r) or of a triangulated surface (verts (n,3), tris (m,3));
-    construction "tube" (radius lambda_over_h * h) or "algorithmic" (interpolation closure)."""
+    construction "tube" (radius lambda_over_h * h) or "algorithmic" (interpolation closure).
+    on_device: build the tube band on the current CUDA device (cpm_build_band_device; the same
+    band bit for bit, its device copies left resident)."""
     s = _capi.cpm_surface(SURFACES[surface], float(R), float(r))
     if surface == "trimesh":
         V = np.ascontiguousarray(verts, dtype=np.float64)
@@ -182,9 +184,14 @@ def cpm_build_band(surface: str, R: float, r: float, h: float, p: int,
         s.tris = T.ctypes.data_as(C.POINTER(C.c_int32))
         s.n_tris = T.shape[0]
     h_out = C.c_void_p()
+    if on_device and construction != "tube":
+        raise ValueError("on_device builds the tube band only")
     if construction == "algorithmic":
         _check(_capi.load().cpm_build_band_algorithmic(C.byref(s), float(h), int(p), C.byref(h_out)),
                "cpm_build_band_algorithmic")
+    elif construction == "tube" and on_device:
+        _check(_capi.load().cpm_build_band_device(C.byref(s), float(h), int(p), float(lambda_over_h),
+                                                  _stream_ptr(stream), C.byref(h_out)), "cpm_build_band_device")
     elif construction == "tube":
         _check(_capi.load().cpm_build_band(C.byref(s), float(h), int(p), float(lambda_over_h),
                                            C.byref(h_out)), "cpm_build_band")

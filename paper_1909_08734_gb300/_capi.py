@@ -74,6 +74,8 @@ _P = C.c_void_p
 _SIGS = {
     "cpm_build_band": (C.c_int, [C.POINTER(cpm_surface), C.c_double, C.c_int, C.c_double, C.POINTER(_P)]),
     "cpm_build_band_algorithmic": (C.c_int, [C.POINTER(cpm_surface), C.c_double, C.c_int, C.POINTER(_P)]),
+    "cpm_build_band_device": (C.c_int, [C.POINTER(cpm_surface), C.c_double, C.c_int, C.c_double, _P,
+                                        C.POINTER(_P)]),
     "cpm_band_info_get": (C.c_int, [_P, C.POINTER(cpm_band_info)]),
     "cpm_band_destroy": (None, [_P]),
     "cpm_partition": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.c_int, C.c_int, C.POINTER(_P)]),

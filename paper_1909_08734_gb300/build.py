@@ -22,7 +22,11 @@ INCLUDE = os.path.join(ROOT, "include")
 
 HOST_SRC = ["host/band.cpp", "host/partition.cpp", "host/local_coo.cpp", "host/ordering.cpp", "capi_host.cpp"]
 CUDA_SRC = ["cuda/apply.cu", "cuda/factor.cu", "cuda/lu_tc.cu", "cuda/trsv.cu", "cuda/krylov.cu",
-            "cuda/stationary.cu", "cuda/selftest.cu", "cuda/probe.cu", "capi_device.cu", "noalloc.cu"]
+            "cuda/stationary.cu", "cuda/selftest.cu", "cuda/probe.cu", "cuda/band_dev.cu", "capi_device.cu",
+            "noalloc.cu"]
+# set decisions (closest points, tube test, weights) computed on the device must match the host
+# code bit for bit: no floating-point contraction there
+NO_FMAD = {"cuda/band_dev.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -71,6 +75,8 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         if _stale(o, [s] + headers):
             cmd = [nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler",
                    "-fPIC,-fopenmp,-ffp-contract=off", "-I", INCLUDE, "-c", s, "-o", o]
+            if src in NO_FMAD:
+                cmd.insert(1, "-fmad=false")
             if ptxas_info:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)

@@ -54,7 +54,8 @@ static cpm_status read_surface(const cpm_surface* surface, cpm::Surface& s) {
 }
 
 static cpm_status build_band_common(const cpm_surface* surface, double h, int p, double lambda_over_h,
-                                    bool algorithmic, cpm_band** out) {
+                                    bool algorithmic, cpm_band** out, bool device = false,
+                                    void* stream = nullptr) {
   if (!surface || !out) {
     cpm::set_error("cpm_build_band: NULL argument");
     return CPM_ERR_INVALID_ARG;
@@ -65,7 +66,9 @@ static cpm_status build_band_common(const cpm_surface* surface, double h, int p,
     cpm_status st = read_surface(surface, s);
     if (st != CPM_OK) return st;
     cpm_band* b = new cpm_band();
-    st = algorithmic ? cpm::build_band_algorithmic(s, h, p, b->b) : cpm::build_band(s, h, p, lambda_over_h, b->b);
+    st = algorithmic ? cpm::build_band_algorithmic(s, h, p, b->b)
+                     : (device ? cpm::build_band_device(s, h, p, lambda_over_h, stream, b->b)
+                               : cpm::build_band(s, h, p, lambda_over_h, b->b));
     if (st != CPM_OK) {
       delete b;
       return st;
@@ -81,6 +84,11 @@ static cpm_status build_band_common(const cpm_surface* surface, double h, int p,
 cpm_status cpm_build_band(const cpm_surface* surface, double h, int p, double lambda_over_h,
                           cpm_band** out) {
   return build_band_common(surface, h, p, lambda_over_h, false, out);
+}
+
+cpm_status cpm_build_band_device(const cpm_surface* surface, double h, int p, double lambda_over_h,
+                                 void* stream, cpm_band** out) {
+  return build_band_common(surface, h, p, lambda_over_h, false, out, true, stream);
 }
 
 cpm_status cpm_build_band_algorithmic(const cpm_surface* surface, double h, int p, cpm_band** out) {

@@ -265,7 +265,7 @@ void point_weights(const double y[3], double h, int p, int32_t base[3], double* 
 static const int NBR_OFF[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0},
                                   {0, 1, 0},  {0, 0, -1}, {0, 0, 1}};
 
-static cpm_status validate_surface(const Surface& s, double h, int p) {
+cpm_status validate_surface(const Surface& s, double h, int p) {
   if (!(h > 0.0) || (p != 2 && p != 3) ||
       (s.kind != CPM_SPHERE && s.kind != CPM_TORUS && s.kind != CPM_TRIMESH) ||
       (s.kind != CPM_TRIMESH && !(s.R > 0.0)) || (s.kind == CPM_TORUS && !(s.r > 0.0 && s.r < s.R))) {
@@ -276,7 +276,7 @@ static cpm_status validate_surface(const Surface& s, double h, int p) {
 }
 
 // Working copy of the surface (mesh bucket grid built) and its bounding box.
-static cpm_status prepare_surface(const Surface& s, double h, Surface& S, double lo[3], double hi[3]) {
+cpm_status prepare_surface(const Surface& s, double h, Surface& S, double lo[3], double hi[3]) {
   S = Surface{s.kind, s.R, s.r, {}};
   if (s.kind == CPM_SPHERE) {
     for (int a = 0; a < 3; ++a) { lo[a] = -s.R; hi[a] = s.R; }
@@ -298,6 +298,32 @@ static cpm_status prepare_surface(const Surface& s, double h, Surface& S, double
   return CPM_OK;
 }
 
+// Mesh bucket cells with a triangle within Chebyshev distance ceil(lam/cell)+1 (separable
+// dilation of the occupied cells along k, then j, then i): a grid node in any other cell is
+// farther than lam from every triangle.
+void mesh_near_cells(const Mesh& M, double lam, std::vector<uint8_t>& near) {
+  const int64_t n0 = M.nc[0], n1 = M.nc[1], n2 = M.nc[2];
+  const int R = (int)std::ceil(lam / M.cell) + 1;
+  std::vector<uint8_t> a((size_t)(n0 * n1 * n2)), b(a.size());
+  for (int64_t c = 0; c < n0 * n1 * n2; ++c) a[c] = M.cell_start[c + 1] > M.cell_start[c];
+  auto dilate = [&](std::vector<uint8_t>& src, std::vector<uint8_t>& dst, int axis) {
+    const int64_t st = axis == 2 ? 1 : (axis == 1 ? n2 : n1 * n2);
+    const int64_t len = axis == 2 ? n2 : (axis == 1 ? n1 : n0);
+#pragma omp parallel for
+    for (int64_t c = 0; c < n0 * n1 * n2; ++c) {
+      const int64_t pos = (c / st) % len;
+      uint8_t v = 0;
+      for (int64_t d = std::max<int64_t>(0, pos - R); d <= std::min<int64_t>(len - 1, pos + R) && !v; ++d)
+        v = src[c + (d - pos) * st];
+      dst[c] = v;
+    }
+  };
+  dilate(a, b, 2);
+  dilate(b, a, 1);
+  dilate(a, b, 0);
+  near.swap(b);
+}
+
 // Grid nodes x with ||x - CP(x)|| <= lam over the bounding box grown by lam, in
 // lexicographic order (slab by slab, i slowest), with their closest points (and triangles).
 static cpm_status enumerate_tube(const Surface& S, const double lo[3], const double hi[3], double h, double lam,
@@ -314,33 +340,10 @@ static cpm_status enumerate_tube(const Surface& S, const double lo[3], const dou
     set_error("cpm_build_band: bounding grid too large");
     return CPM_ERR_INVALID_ARG;
   }
-  // mesh: cells with a triangle within Chebyshev distance ceil(lam/cell)+1 ("near"); a node in
-  // any other cell is farther than lam from every triangle
+  // mesh: only nodes in cells near a triangle can be within lam of the surface
   std::vector<uint8_t> near;
   const Mesh& M = S.mesh;
-  if (mesh) {
-    const int64_t n0 = M.nc[0], n1 = M.nc[1], n2 = M.nc[2];
-    const int R = (int)std::ceil(lam / M.cell) + 1;
-    std::vector<uint8_t> a((size_t)(n0 * n1 * n2)), b(a.size());
-    for (int64_t c = 0; c < n0 * n1 * n2; ++c) a[c] = M.cell_start[c + 1] > M.cell_start[c];
-    // separable dilation along k, then j, then i
-    auto dilate = [&](std::vector<uint8_t>& src, std::vector<uint8_t>& dst, int axis) {
-      const int64_t st = axis == 2 ? 1 : (axis == 1 ? n2 : n1 * n2);
-      const int64_t len = axis == 2 ? n2 : (axis == 1 ? n1 : n0);
-#pragma omp parallel for
-      for (int64_t c = 0; c < n0 * n1 * n2; ++c) {
-        const int64_t pos = (c / st) % len;
-        uint8_t v = 0;
-        for (int64_t d = std::max<int64_t>(0, pos - R); d <= std::min<int64_t>(len - 1, pos + R) && !v; ++d)
-          v = src[c + (d - pos) * st];
-        dst[c] = v;
-      }
-    };
-    dilate(a, b, 2);
-    dilate(b, a, 1);
-    dilate(a, b, 0);
-    near.swap(b);
-  }
+  if (mesh) mesh_near_cells(M, lam, near);
   std::vector<std::vector<int32_t>> slab_ijk(ni), slab_tri(ni);
   std::vector<std::vector<double>> slab_cp(ni);
 #pragma omp parallel

@@ -112,6 +112,15 @@ void envelope(const LocalCOO& L, int T, std::vector<int32_t>& first, std::vector
               std::vector<int32_t>& pend);
 
 cpm_status build_band(const Surface& s, double h, int p, double lam_over_h, Band& out);
+// Pieces of the band construction shared with the device build: argument checks, the working
+// surface (mesh bucket grid) and its bounding box, and the mesh cells near a triangle.
+cpm_status validate_surface(const Surface& s, double h, int p);
+cpm_status prepare_surface(const Surface& s, double h, Surface& S, double lo[3], double hi[3]);
+void mesh_near_cells(const Mesh& M, double lam, std::vector<uint8_t>& near);
+// The same band as build_band, built on the current CUDA device (closest points, tube test,
+// canonical order, ghosts, neighbour table and interpolation data); the host arrays are
+// filled from the device and the device copies stay resident for the operators.
+cpm_status build_band_device(const Surface& s, double h, int p, double lam_over_h, void* stream, Band& out);
 // Algorithmic band: the smallest node set containing the grid nodes within h of the surface
 // and the interpolation stencils of CP(x) for its nodes and their 6-neighbours.
 cpm_status build_band_algorithmic(const Surface& s, double h, int p, Band& out);
