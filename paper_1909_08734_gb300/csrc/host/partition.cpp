@@ -46,10 +46,6 @@ void rcb(const Band& B, const std::vector<int64_t>& w, std::vector<int32_t>& lab
     int axis = 0;
     if (ext[1] > ext[axis]) axis = 1;
     if (ext[2] > ext[axis]) axis = 2;
-    std::sort(job.idx.begin(), job.idx.end(), [&](int32_t a, int32_t b) {
-      double va = B.cp[3 * (size_t)a + axis], vb = B.cp[3 * (size_t)b + axis];
-      return va < vb || (va == vb && a < b);
-    });
     const int PL = P / 2;
     int64_t WL = 0, W = 0;
     for (int l = job.l0; l < job.l1; ++l) {
@@ -58,6 +54,13 @@ void rcb(const Band& B, const std::vector<int64_t>& w, std::vector<int32_t>& lab
     }
     const int64_t n = (int64_t)job.idx.size();
     const int64_t nL = (n * WL) / W;
+    // the first nL points in the order (CP[axis], index), a total order: a selection gives the
+    // same halves as a full sort (each half is ordered again by its own split)
+    if (nL > 0 && nL < n)
+      std::nth_element(job.idx.begin(), job.idx.begin() + nL, job.idx.end(), [&](int32_t a, int32_t b) {
+        double va = B.cp[3 * (size_t)a + axis], vb = B.cp[3 * (size_t)b + axis];
+        return va < vb || (va == vb && a < b);
+      });
     Job L, R;
     L.idx.assign(job.idx.begin(), job.idx.begin() + nL);
     R.idx.assign(job.idx.begin() + nL, job.idx.end());
