@@ -6,6 +6,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "cuda/kernels.h"
@@ -242,15 +243,28 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   cpm_status st = ensure_band_on_device(B, pc->device);
   if (st != CPM_OK) return st;
 
-  // ---- host: local operators in coordinate form ----
+  // ---- host, per subdomain in one parallel loop: the local operator in coordinate form, its
+  // fill-reducing order (reverse Cuthill-McKee) and the tile envelope of its factors ----
   std::vector<cpm::LocalCOO> coo(ns);
   std::vector<cpm_status> sts(ns, CPM_OK);
   std::vector<std::string> errs(ns);
+  std::vector<std::vector<int32_t>> inv_order(ns), env_first(ns), env_last(ns), env_pend(ns);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int j = 0; j < ns; ++j) {
     try {
       sts[j] = cpm::build_local_coo(B, P, c, transmission, alpha, alpha_x, j, coo[j], false);
-      if (sts[j] != CPM_OK) errs[j] = cpm_last_error();
+      if (sts[j] != CPM_OK) {
+        errs[j] = cpm_last_error();
+        continue;
+      }
+      std::vector<int32_t> perm;
+      cpm::rcm_order(coo[j], perm);
+      std::vector<int32_t>& inv = inv_order[j];
+      inv.resize(coo[j].n);
+      for (int64_t k = 0; k < coo[j].n; ++k) inv[perm[k]] = (int32_t)k;
+      for (auto& r : coo[j].row) r = inv[r];
+      for (auto& cc : coo[j].col) cc = inv[cc];
+      cpm::envelope(coo[j], (int)((coo[j].n + TILE - 1) / TILE), env_first[j], env_last[j], env_pend[j]);
     } catch (const std::bad_alloc&) {
       sts[j] = CPM_ERR_OOM;
       errs[j] = "out of host memory building local operators";
@@ -261,18 +275,6 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
       cpm::set_error(errs[j]);
       return sts[j];
     }
-  // ---- host: fill-reducing order of every local operator (reverse Cuthill-McKee) ----
-  std::vector<std::vector<int32_t>> inv_order(ns);
-#pragma omp parallel for schedule(dynamic, 1)
-  for (int j = 0; j < ns; ++j) {
-    std::vector<int32_t> perm;
-    cpm::rcm_order(coo[j], perm);
-    std::vector<int32_t>& inv = inv_order[j];
-    inv.resize(coo[j].n);
-    for (int64_t k = 0; k < coo[j].n; ++k) inv[perm[k]] = (int32_t)k;
-    for (auto& r : coo[j].row) r = inv[r];
-    for (auto& cc : coo[j].col) cc = inv[cc];
-  }
   pc->meta.resize(ns);
   pc->n_local.resize(ns);
   pc->n_sigma.resize(ns);
@@ -306,11 +308,12 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
 #pragma omp parallel for schedule(dynamic, 1)
   for (int j = 0; j < ns; ++j) {
     const SubMeta& m = pc->meta[j];
-    std::vector<int32_t> f, l, pe;
-    cpm::envelope(coo[j], m.T, f, l, pe);
-    std::copy(f.begin(), f.end(), h_first.begin() + m.row_off);
-    std::copy(l.begin(), l.end(), h_last.begin() + m.row_off);
-    std::copy(pe.begin(), pe.end(), h_pend.begin() + (size_t)j * t_max);
+    std::copy(env_first[j].begin(), env_first[j].end(), h_first.begin() + m.row_off);
+    std::copy(env_last[j].begin(), env_last[j].end(), h_last.begin() + m.row_off);
+    std::copy(env_pend[j].begin(), env_pend[j].end(), h_pend.begin() + (size_t)j * t_max);
+    std::vector<int32_t>().swap(env_first[j]);
+    std::vector<int32_t>().swap(env_last[j]);
+    std::vector<int32_t>().swap(env_pend[j]);
   }
   std::vector<int32_t> step_rows(t_max, 64);
   for (int j = 0; j < ns; ++j)
@@ -320,8 +323,9 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   const size_t wbytes = fp64 ? 8 : 4;
 
   // element offsets of every entry in the tiled layout
-  std::vector<int64_t> h_off(nnz);
-  std::vector<double> h_val(nnz);
+  // not value-initialised: the parallel loop below writes (and first-touches) every entry
+  std::unique_ptr<int64_t[]> h_off(new int64_t[nnz > 0 ? nnz : 1]);
+  std::unique_ptr<double[]> h_val(new double[nnz > 0 ? nnz : 1]);
   {
     std::vector<int64_t> start(ns + 1, 0);
     for (int j = 0; j < ns; ++j) start[j + 1] = start[j] + (int64_t)coo[j].val.size();
@@ -393,8 +397,8 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   CK(cudaMemcpyAsync(d_unk, unknowns.data(), 4 * pc->sum_n, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_own, own.data(), 4 * pc->sum_n, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_unk_off, unk_off.data(), 8 * ns, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d_off, h_off.data(), 8 * nnz, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d_val, h_val.data(), 8 * nnz, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_off, h_off.get(), 8 * nnz, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_val, h_val.get(), 8 * nnz, cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(pc->status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(pc->status + 1, 0x7f, sizeof(int), s));
 
