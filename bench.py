@@ -31,7 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ORAS-GMRES time-to-1e-8 residual, mixed vs FP64 (solves/s, HBM GB/s); p50/p99"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "trsv_fp32_sphere_h0025.md")
+# ncu summaries of the solve kernel's DRAM traffic at full size, per (workload, factor precision)
+PROFILE_SUMMARIES = {("sphere_h0025", "fp32"): os.path.join(ROOT, "profiles", "trsv_fp32_sphere_h0025.md"),
+                     ("torus_h00125", "bf16"): os.path.join(ROOT, "profiles", "trsv_bf16_torus_h00125.md")}
 
 
 def _dist():
@@ -111,13 +113,15 @@ def _file_sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it still matches the kernel."""
+def _profiled_traffic(workload, precision):
+    """DRAM bytes per launch from the committed ncu summary of this workload and precision, if
+    there is one and it still matches the kernel source."""
     src = os.path.join(ROOT, "paper_1909_08734_gb300", "csrc", "cuda", "trsv.cu")
-    if not os.path.exists(PROFILE_SUMMARY):
+    summary = PROFILE_SUMMARIES.get((workload, precision))
+    if summary is None or not os.path.exists(summary):
         return None
     fields = {}
-    for line in open(PROFILE_SUMMARY):
+    for line in open(summary):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             fields[k.strip()] = v.strip()
@@ -481,7 +485,7 @@ def run_native(args):
         achieved = head_bytes / (apply_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4),
-                    "traffic": _profiled_traffic() if (head == "fp32" and wl.name == "sphere_h0025") else None,
+                    "traffic": _profiled_traffic(wl.name, head),
                     "kernel": "trsv_kernel<%s>" % ("float,float" if head == "fp32" else "bf16,float"),
                     "launch_ms": round(apply_ms, 4), "algorithmic_bytes": head_bytes, "peak_source": peak_kind}
     # operator apply y = A x (FP64, matrix-free): extension values at every band node, then the
