@@ -453,9 +453,10 @@ def run_native(args):
                                                   1024, 8, 4096, latency=True)
     peak, peak_kind = _peaks()
     # bytes one application must stream: the off-diagonal factor tiles inside the tile
-    # envelope (storage precision), two inverted diagonal blocks per tile row (compute
-    # precision), the restricted residual reads and the prolonged writes
-    tiles_off, tiles_inv = info["solve_offdiag_tiles"] * 4096, 2 * info["tile_rows"] * 4096
+    # envelope (storage precision), the two inverted diagonal blocks of every tile row, each
+    # stored as its triangle of 64 * 65 / 2 entries (compute precision), the restricted residual
+    # reads and the prolonged writes
+    tiles_off, tiles_inv = info["solve_offdiag_tiles"] * 4096, 2 * info["tile_rows"] * 2080
     vec_bytes = 8 * info["sum_sigma"] + 8 * n
     store = {"fp32": 4, "bf16": 2, "fp64": 8}
     comp = {"fp32": 4, "bf16": 4, "fp64": 8}

@@ -498,6 +498,7 @@ cpm_status setup_impl(oras_precond* pc, const cpm::Band& B, const cpm::Partition
   CK(legacy_fence());
   // chain tiles of the solves: L_{I,I-1} and U_{I,I+1} premultiplied by the diagonal inverses
   CK(launch_chain_tiles(work, fp64, pc->d_meta, ns, t_max, inv, d_tlo, d_thi, s));
+  CK(launch_pack_inverse(inv, fp64, n_trow, s));       // the solves stream the triangles only
   CK(cudaStreamSynchronize(s));
   int hst2[2] = {0, 0};
   CK(cudaMemcpy(hst2, pc->status, 2 * sizeof(int), cudaMemcpyDeviceToHost));

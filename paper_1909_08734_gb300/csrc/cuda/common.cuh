@@ -36,6 +36,12 @@ struct SubMeta {
 // ---- element offsets inside one 64 x 64 tile ----------------------------------------
 // FP64 / BF16 storage: plain column-major.
 __host__ __device__ __forceinline__ int off_plain(int i, int j) { return j * TILE + i; }
+// Packed diagonal-block inverses: each triangle stored column by column at the start of its
+// 64 x 64 slot, INV_PACKED entries.  L^{-1} (unit lower) keeps rows r >= c of column c,
+// U^{-1} (upper) rows r <= c; the index of (r, c) inside its triangle:
+constexpr int INV_PACKED = TILE * (TILE + 1) / 2;
+__host__ __device__ __forceinline__ int inv_lower_index(int r, int c) { return c * TILE - c * (c - 1) / 2 + (r - c); }
+__host__ __device__ __forceinline__ int inv_upper_index(int r, int c) { return c * (c + 1) / 2 + r; }
 // FP32 storage: sixteen 1 KB atoms of 32 rows x 8 columns (atom (i/32, j/8) at
 // ((i/32)*8 + j/8) KB); inside an atom, column j%8 is a 128-byte line of 32 consecutive
 // rows whose 16-byte chunks are XOR-swizzled with the line index.  This is the canonical

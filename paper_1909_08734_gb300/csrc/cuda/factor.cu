@@ -796,6 +796,34 @@ cudaError_t launch_chain_tiles(void* a, int fp64, const SubMeta* meta, int n_sub
   return cudaGetLastError();
 }
 
+// Packs every diagonal-block inverse into its triangle at the start of its slot (slot 2 trow:
+// L^{-1}, slot 2 trow + 1: U^{-1}; INV_PACKED entries each), after the chain tiles have used
+// the full tiles: the solves then stream half a tile per inverse.
+template <typename C>
+__global__ void __launch_bounds__(64) pack_inverse_kernel(C* inv) {
+  const int64_t slot = blockIdx.x;
+  const bool upper = (slot & 1) != 0;
+  C* t = inv + slot * (int64_t)TILE_ELEMS;
+  __shared__ C X[TILE_ELEMS];
+  for (int e = threadIdx.x; e < TILE_ELEMS; e += 64) X[e] = t[e];
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (upper) {
+    for (int r = 0; r <= c; ++r) t[inv_upper_index(r, c)] = X[off_plain(r, c)];
+  } else {
+    for (int r = c; r < TILE; ++r) t[inv_lower_index(r, c)] = X[off_plain(r, c)];
+  }
+}
+
+cudaError_t launch_pack_inverse(void* inv, int fp64, int64_t n_tile_rows, cudaStream_t s) {
+  const int64_t slots = 2 * n_tile_rows;
+  if (slots <= 0) return cudaSuccess;
+  if (slots > 2147483647) return cudaErrorInvalidValue;
+  if (fp64) pack_inverse_kernel<double><<<(unsigned)slots, 64, 0, s>>>((double*)inv);
+  else pack_inverse_kernel<float><<<(unsigned)slots, 64, 0, s>>>((float*)inv);
+  return cudaGetLastError();
+}
+
 __global__ void pack_bf16_kernel(const float* __restrict__ a, __nv_bfloat16* __restrict__ out,
                                  int64_t n_tiles) {
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {

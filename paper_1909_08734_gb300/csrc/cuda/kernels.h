@@ -120,6 +120,8 @@ cudaError_t launch_pack_bf16(const float* a, __nv_bfloat16* out, int64_t n_tiles
 // row whose envelope holds them (the solves' chain tiles); inv as from launch_diag_inverse.
 cudaError_t launch_chain_tiles(void* a, int fp64, const SubMeta* meta, int n_sub, int t_max, const void* inv,
                                const int32_t* tlo, const int32_t* thi, cudaStream_t s);
+// Packs the diagonal-block inverses into their triangles (after launch_chain_tiles)
+cudaError_t launch_pack_inverse(void* inv, int fp64, int64_t n_tile_rows, cudaStream_t s);
 cudaError_t launch_diag_inverse(const void* a, int fp64, const SubMeta* meta, int n_sub, int t_max,
                                 void* inv, cudaStream_t s);
 

@@ -140,6 +140,28 @@ __device__ __forceinline__ Item decode(const TrsvDev& t, int idx) {
   return e;
 }
 
+// p4[q][u] += Inv[r][c] xb[q][c] over the thread's 32 columns c (half HALF of the row) of a
+// packed triangular inverse (UPPER: U^{-1}, else L^{-1}); p0 / p1: the stages holding entries
+// [0, CPS) and [CPS, INV_PACKED).  Column and direction are compile-time here, so each packed
+// index is r plus a constant (an immediate offset); every such index lies inside the triangle's
+// INV_PACKED entries, so the loads need no guard and the entries outside the triangle are
+// replaced by zero after the load.
+template <int HALF, bool UPPER, int CPS, int NR, typename C>
+__device__ __forceinline__ void packed_inverse_product(const C* p0, const C* p1, int r, const C (*xb)[64],
+                                                       C (&p4)[NR][4]) {
+#pragma unroll
+  for (int c0 = 32 * HALF; c0 < 32 * HALF + 32; c0 += 4)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int col = c0 + u;
+      const int el = UPPER ? inv_upper_index(r, col) : inv_lower_index(r, col);
+      const C v = (CPS >= INV_PACKED || el < CPS) ? p0[el] : p1[el - CPS];
+      const C a = (UPPER ? r <= col : r >= col) ? v : (C)0;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) p4[q][u] += a * xb[q][col];
+    }
+}
+
 // NR right-hand sides share every streamed tile (columns NR of IndirectVec r_in / z_out);
 // tagged words are laid out (row, rhs) with NR words per row.
 template <typename S, typename C, int NR>
@@ -152,6 +174,10 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   constexpr int CPS = STAGE / sizeof(C);                      // C values per stage
   constexpr int NSTAGE = ring_stages<S>();
   static_assert(PIECES >= 1 && PIECES <= 2 && NSTAGE >= PIECES, "ring too small");
+  // a packed inverse (one triangle, INV_PACKED entries) spans PIECES stages, the last one partly
+  constexpr uint32_t INV_BYTES = (uint32_t)(sizeof(C) * INV_PACKED);
+  static_assert(INV_BYTES > (PIECES - 1) * STAGE && INV_BYTES <= PIECES * STAGE && INV_BYTES % 16 == 0,
+                "packed inverse does not fill its stages");
   __shared__ __align__(8) uint64_t bar[NSTAGE];
   __shared__ C yb[2][NR][64];                                 // solved pieces, double-buffered
   __shared__ C xb[NR][64];
@@ -186,7 +212,6 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
   auto issue_load = [&](const Item& e, int l) {
     const int st = lc % NSTAGE;
     unsigned char* dst = smem + (size_t)st * STAGE;
-    mbar_expect_tx(&bar[st], STAGE);
     const SubMeta m = t.meta[e.j];
     // load order of a diagonal item: off-diagonal tiles but the chain tile, the inverse
     // pieces, the chain tile (the neighbouring row's, premultiplied by the inverse)
@@ -203,11 +228,14 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
     if (tq >= 0) {
       const int q = e.q0 + tq;
       const int J = e.bwd ? e.jb - q : e.jb + q;
+      mbar_expect_tx(&bar[st], STAGE);
       bulk_g2s_hint(dst, tiles + tile_base(m, e.I, J), STAGE, &bar[st], l2_pol);
     } else {
       const int64_t trow = (m.row_off >> 6) + e.I;
       const unsigned char* it = (const unsigned char*)(inv + (trow * 2 + e.bwd) * (int64_t)TILE_ELEMS);
-      bulk_g2s_hint(dst, it + (size_t)piece * STAGE, STAGE, &bar[st], l2_pol);
+      const uint32_t bytes = min(STAGE, INV_BYTES - (uint32_t)piece * STAGE);   // the packed triangle only
+      mbar_expect_tx(&bar[st], bytes);
+      bulk_g2s_hint(dst, it + (size_t)piece * STAGE, bytes, &bar[st], l2_pol);
     }
     ++lc;
   };
@@ -376,16 +404,18 @@ __global__ void __launch_bounds__(TRSV_THREADS) trsv_kernel(TrsvDev t, IndirectV
       for (int q = 0; q < NR; ++q)
 #pragma unroll
         for (int u = 0; u < 4; ++u) p4[q][u] = (C)0;
-#pragma unroll
-      for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 4)
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int el = (c0 + u) * 64 + r;               // column-major inverse element
-          const C* piece = (const C*)(smem + (size_t)((cc + el / CPS) % NSTAGE) * STAGE);
-          const C a = piece[el % CPS];
-#pragma unroll
-          for (int q = 0; q < NR; ++q) p4[q][u] += a * xb[q][c0 + u];
+      {
+        // the packed inverse: stage cc (and cc + 1 when it spans two stages)
+        const C* p0 = (const C*)(smem + (size_t)(cc % NSTAGE) * STAGE);
+        const C* p1 = (const C*)(smem + (size_t)((cc + 1) % NSTAGE) * STAGE);
+        if (half == 0) {
+          if (e.bwd) packed_inverse_product<0, true, CPS, NR>(p0, p1, r, xb, p4);
+          else packed_inverse_product<0, false, CPS, NR>(p0, p1, r, xb, p4);
+        } else {
+          if (e.bwd) packed_inverse_product<1, true, CPS, NR>(p0, p1, r, xb, p4);
+          else packed_inverse_product<1, false, CPS, NR>(p0, p1, r, xb, p4);
         }
+      }
 #pragma unroll
       for (int q = 0; q < NR; ++q) red2[q][tid] = (p4[q][0] + p4[q][1]) + (p4[q][2] + p4[q][3]);
       __syncthreads();
