@@ -384,6 +384,16 @@ cpm_status cpm_vec_axpby(int64_t n, double a, const double* x_dev, double b, dou
  * completed, INVALID_ARG or CUDA otherwise. */
 cpm_status cpm_selftest_bounded_wait(oras_precond* pc, double limit_s, void* stream);
 
+/* Failure-detection check of the FGMRES breakdown report; no counterpart in the paper.  Makes
+ * pc's operator the zero matrix (both coefficients of the stabilised operator set to 0, so
+ * cpm_op_apply, cpm_gmres_solve and oras_stationary_solve then apply A x = 0 exactly for
+ * finite x; the preconditioner is unchanged) and drops the captured iteration graphs.  A
+ * solve with a nonzero right-hand side then meets A z_0 = 0 in its first Arnoldi step: the
+ * Hessenberg matrix is singular with the residual still at ||f||, and cpm_gmres_solve reports
+ * CPM_ERR_BREAKDOWN with u unchanged.  Irreversible for this handle (destroy it afterwards).
+ * Synchronises the current device.  Errors: INVALID_ARG (null handle), CUDA. */
+cpm_status cpm_selftest_zero_operator(oras_precond* pc);
+
 /* Failure-detection check of the zero-pivot report; no counterpart in the paper.  Runs the
  * set-up of oras_setup with the same arguments, but after the local matrices are assembled
  * on the device, local column 0 of subdomain `subdomain` is set to zero in every row (as if

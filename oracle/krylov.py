@@ -17,6 +17,13 @@ One cycle from x with r = f - A x, beta = ||r||:
       stop the cycle when |g[k+1]| <= tol ||f||, at m steps, or at breakdown (||w|| = 0)
   y = H[:k+1, :k+1]^{-1} g[:k+1] (back substitution),  x = x + Z_k y
 Then the true residual ||f - A x|| decides convergence (<= tol ||f||); otherwise restart.
+
+Breakdown (a reading; the paper never meets it): ||w|| = 0 means A z_k lies in the span of
+the basis.  If the rotated diagonal rho is nonzero the least-squares problem is solved
+exactly (a "happy" breakdown) and the cycle ends as usual.  If rho = 0 the Hessenberg matrix
+is singular: column k is left out (the update uses the first k columns) and the solve stops.
+In both cases a true residual still above the tolerance ends the solve with breakdown set,
+since restarting from the same residual would build the same basis again.
 """
 from __future__ import annotations
 
@@ -32,6 +39,7 @@ class GmresResult:
     relres: float
     converged: bool
     history: list          # |g_{k+1}| / ||f|| after every inner step
+    breakdown: bool = False
 
 
 def fgmres(A_apply, M_apply, f: np.ndarray, tol: float, restart: int = 50,
@@ -57,6 +65,7 @@ def fgmres(A_apply, M_apply, f: np.ndarray, tol: float, restart: int = 50,
         g[0] = beta
         V[0] = r / beta
         k_done = 0
+        broke = False
         for k in range(m):
             Z[k] = M_apply(V[k])
             w = A_apply(Z[k])
@@ -76,15 +85,23 @@ def fgmres(A_apply, M_apply, f: np.ndarray, tol: float, restart: int = 50,
                 H[i, k] = t
             a, b = H[k, k], H[k + 1, k]
             rho = np.sqrt(a * a + b * b)
+            total += 1
+            if rho == 0.0:                 # singular Hessenberg: drop column k
+                broke = True
+                k_done = k
+                hist.append(abs(g[k]) / nf)
+                break
             cs[k], sn[k] = a / rho, b / rho
             H[k, k] = rho
             H[k + 1, k] = 0.0
             g[k + 1] = -sn[k] * g[k]
             g[k] = cs[k] * g[k]
-            total += 1
             k_done = k + 1
             hist.append(abs(g[k + 1]) / nf)
-            if abs(g[k + 1]) <= tol * nf or hn == 0.0 or total >= max_it:
+            if hn == 0.0:
+                broke = True
+                break
+            if abs(g[k + 1]) <= tol * nf or total >= max_it:
                 break
             if stop_after is not None and total >= stop_after:
                 break
@@ -101,3 +118,5 @@ def fgmres(A_apply, M_apply, f: np.ndarray, tol: float, restart: int = 50,
             return GmresResult(x, total, rel, True, hist)
         if total >= max_it or beta == 0.0:
             return GmresResult(x, total, rel, False, hist)
+        if broke:
+            return GmresResult(x, total, rel, False, hist, True)

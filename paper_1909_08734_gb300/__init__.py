@@ -429,5 +429,11 @@ def cpm_selftest_bounded_wait(pc: Preconditioner, limit_s: float = 0.2, stream=N
     return int(_capi.load().cpm_selftest_bounded_wait(pc.handle, float(limit_s), _stream_ptr(stream)))
 
 
+def cpm_selftest_zero_operator(pc: Preconditioner) -> None:
+    """Make pc's operator the zero matrix (breakdown self-test; the handle is not usable for
+    real solves afterwards)."""
+    _check(_capi.load().cpm_selftest_zero_operator(pc.handle), "cpm_selftest_zero_operator")
+
+
 def status_string(code: int) -> str:
     return _capi.load().cpm_status_string(int(code)).decode()

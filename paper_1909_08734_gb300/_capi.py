@@ -110,6 +110,7 @@ _SIGS = {
                                         C.POINTER(cpm_gmres_result), _P]),
     "cpm_vec_axpby": (C.c_int, [C.c_int64, C.c_double, _P, C.c_double, _P, _P]),
     "cpm_selftest_bounded_wait": (C.c_int, [_P, C.c_double, _P]),
+    "cpm_selftest_zero_operator": (C.c_int, [_P]),
     "oras_setup_selftest_singular": (C.c_int, [_P, _P, C.c_double, C.c_int, C.c_double, C.c_double, C.c_int,
                                                C.c_int, _P]),
     "cpm_probe_fp64": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),

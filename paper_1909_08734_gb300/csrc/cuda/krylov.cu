@@ -530,7 +530,11 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
   // that it does not wait for the square root of ||w||
   const double hn = sqrt(tot);
   const double rho = sqrt(fma(cur, cur, tot));
-  const double c = cur / rho, sv = hn / rho;
+  // rho = 0 (then ||w|| = 0 too): A z_k lies in span(V_0 .. V_{k-1}) and the rotated column has
+  // a zero diagonal, so the Hessenberg matrix is singular; the rotation is left as the identity
+  // and column k is kept out of the least-squares solve below
+  const bool singular = rho == 0.0;
+  const double c = singular ? 1.0 : cur / rho, sv = singular ? 0.0 : hn / rho;
   st[L.cs() + k] = c;
   st[L.sn() + k] = sv;
   st[L.H(k, k)] = rho;
@@ -546,6 +550,10 @@ __global__ void __launch_bounds__(ST) arn_upd2_kernel(GmresDev g) {
   const double est = fabs(-sv * gk);
   const double nf = pre[385], tol = pre[386];
   bool stop = est <= tol * nf || hn == 0.0 || k + 1 >= g.m || total >= prei[1];
+  // ||w|| = 0 ends the cycle (hn == 0 above); the restart test then reports CPM_ERR_BREAKDOWN
+  // unless the true residual meets the tolerance.  A singular Hessenberg matrix updates u with
+  // its first k columns only.
+  if (singular) ist[I_KDONE] = k;
   if (!isfinite(hn) || !isfinite(rho) || !isfinite(est)) {
     ist[I_STATUS] = CPM_ERR_NAN;
     stop = true;

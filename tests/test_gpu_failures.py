@@ -7,6 +7,10 @@
   solver, and the next solve on the same handle succeeds.
 * A zero pivot (one local column zeroed by the set-up self-test) is reported as
   CPM_ERR_SINGULAR with the subdomain it belongs to.
+* A singular Hessenberg matrix (the operator made the zero matrix by a self-test, so that
+  A z_0 = 0 while the residual is still ||f||) is reported as CPM_ERR_BREAKDOWN after one
+  iteration with u unchanged, on its own and next to a zero right-hand side in a lock-step
+  batch, with and without the captured iteration graph.
 """
 import time
 
@@ -78,3 +82,34 @@ def test_zero_pivot_is_reported_with_its_subdomain(prec):
     f = _f(pc)
     u = torch.zeros_like(f)
     assert G.cpm_gmres_solve(pc, f, u, tol=1e-8)[0]["status"] == 0
+
+
+@pytest.mark.parametrize("nrhs,use_graph,zero_second", [(1, True, False), (1, False, False), (2, True, True),
+                                                         (2, False, False)])
+def test_singular_hessenberg_is_reported_as_breakdown(nrhs, use_graph, zero_second):
+    band = G.cpm_build_band("sphere", 1.0, 0.0, 0.1, 3)
+    part = G.cpm_partition(band, 8, None, 2)
+    pc = G.oras_setup(band, part, 1.0, "oras", 4.0, 40.0, "fp32")
+    f1 = _f(pc)
+    x = torch.linspace(-1.0, 1.0, pc.n_active, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    G.cpm_op_apply(pc, x, y)
+    assert torch.count_nonzero(y).item() > 0
+    G.cpm_selftest_zero_operator(pc)
+    G.cpm_op_apply(pc, x, y)
+    assert torch.count_nonzero(y).item() == 0     # A = 0 exactly
+    rows = [f1] + [torch.zeros_like(f1) if zero_second else 2.0 * f1][: nrhs - 1]
+    f = torch.cat(rows).contiguous()
+    u = torch.zeros_like(f)
+    res = G.cpm_gmres_solve(pc, f, u, nrhs=nrhs, tol=1e-8, use_graph=use_graph, raise_on_failure=False)
+    for q, r in enumerate(res):
+        if q == 1 and zero_second:                # ||f|| = 0: converged before the first step
+            assert r["status"] == 0 and r["iterations"] == 0, r
+            continue
+        assert r["status"] == _capi.CPM_ERR_BREAKDOWN, r
+        assert r["iterations"] == 1, r
+        assert abs(r["relres"] - 1.0) < 1e-14, r  # nothing was updated: r = f
+    assert torch.count_nonzero(u).item() == 0
+    with pytest.raises(G.CpmError) as e:
+        G.cpm_gmres_solve(pc, f, u, nrhs=nrhs, tol=1e-8, use_graph=use_graph)
+    assert e.value.status == _capi.CPM_ERR_BREAKDOWN
