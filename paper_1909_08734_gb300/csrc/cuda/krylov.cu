@@ -148,6 +148,7 @@ struct VStream {
     const uint32_t bytes = (uint32_t)((rows(q) * 8 + 15) & ~15);
     const int i0 = batch(q) * VB, cnt = count(q);
     mbar_expect_tx(&bar[q & 1], bytes * (uint32_t)cnt);
+    if (bytes == 0) return;             // a block without rows: the arrival completes the phase
     const double* src = Vb + (int64_t)tile(q) * TR;
     for (int u = 0; u < cnt; ++u) bulk_g2s(buf(q) + u * TR, src + (int64_t)(i0 + u) * ld, bytes, &bar[q & 1]);
   }
@@ -170,12 +171,18 @@ __device__ __forceinline__ VStream make_stream(const GmresDev& g, const double* 
   return v;
 }
 
-// Start of a step kernel's stream: barriers initialised, the first two batches in flight.
+// Start of a step kernel's stream: barriers initialised, the first two batches in flight.  The
+// block barrier between the initialisation and the copies orders every thread's first wait
+// after the initialisation (a wait on an mbarrier that thread 0 has not yet initialised is
+// undefined); the copies are issued after it, so the other threads go on meanwhile.
 __device__ __forceinline__ void stream_begin(const VStream& vs, uint64_t* bar) {
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
     fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     vs.issue(0);
     vs.issue(1);
   }
