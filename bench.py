@@ -786,8 +786,7 @@ def main():
     ap.add_argument("--serving-precisions", default="fp32,fp64")
     ap.add_argument("--serving-trace", default="", help="file for the serving loop's per-batch trace")
     ap.add_argument("--serving-slots", default="1",
-                    help="concurrent batches (own stream and host thread each; more than one is not "
-                         "validated); one run per value")
+                    help="concurrent batches (own stream and host thread each); one run per value")
     ap.add_argument("--peaks", action="store_true",
                     help="FP64 FMA peak / latency probe sweep (the FP64 roofline denominator)")
     ap.add_argument("--subdomain-table", action="store_true",

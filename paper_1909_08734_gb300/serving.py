@@ -9,9 +9,7 @@ factorisation.  The server
   resident in HBM (per surface, h, c), least recently used first out;
 * runs `slots` batches at once (default 1): each slot owns a CUDA stream and a host thread,
   and one operator serves one batch at a time, as a handle is not thread-safe.  More than one
-  slot lets batches on different operators overlap on the device, but that mode faulted the
-  device in runs of the mixed serving stream with four slots, for a cause not yet found; it is
-  not validated and stays off unless asked for;
+  slot lets batches on different operators overlap on the device;
 * admits continuously: whenever a slot is free, the oldest queued request whose operator is
   not busy picks the operator, and every queued plain request for the same operator joins its
   batch (one lock-step multi-rhs cpm_gmres_solve); requests arriving meanwhile wait for the

@@ -5,6 +5,9 @@
 * a request's solutions are bit-identical served alone and inside a mix that forces
   batching with other requests and evictions of its operator;
 * a request that cannot fit the budget fails with CPM_ERR_BUDGET, the rest are served;
+* continuous batching: batches on different operators run at once in separate slots (own
+  stream and host thread), their CUDA-event intervals overlap on the device, and each result
+  is bit-identical to serving it alone;
 * served solutions agree with the oracle's sparse direct solve (A from the paper's
   discretisation, Eq. impLapBel), and a backward-Euler chain with c = 1/dt agrees with the
   oracle's chain u_n = A^{-1}(c u_{n-1}) to the solve tolerance times cond(A).
@@ -16,7 +19,7 @@ import scipy.sparse.linalg as spla
 torch = pytest.importorskip("torch")
 import paper_1909_08734_gb300 as G  # noqa: E402
 from paper_1909_08734_gb300 import _capi  # noqa: E402
-from paper_1909_08734_gb300.serving import Request, Server, summarize  # noqa: E402
+from paper_1909_08734_gb300.serving import Request, Server, overlap_seconds, summarize  # noqa: E402
 from oracle import band as ob  # noqa: E402
 from oracle import geometry, interp, operator  # noqa: E402
 from workloads import perturbed_icosphere, smooth_rhs  # noqa: E402
@@ -101,6 +104,24 @@ def test_alone_and_mixed_results_are_bit_identical():
     assert np.array_equal(mixed.u, alone.u)
     assert mixed.iterations == alone.iterations
     b.close()
+
+
+def test_batches_on_different_operators_overlap_on_the_device():
+    specs = [("sphere", 0.05, 1.0, 4, 41), ("torus", 0.05, 2.0, 4, 43), ("sphere", 0.05, 7.0, 2, 45)]
+    alone = {}
+    for k, sp in enumerate(specs):
+        s = _server(precision="fp32", slots=1)
+        alone[k] = s.serve([_req(s, k, *sp)], realtime=False)[0]
+        s.close()
+    s = _server(precision="fp32", slots=3)
+    out = {r.rid: r for r in s.serve([_req(s, k, *sp) for k, sp in enumerate(specs)], realtime=False)}
+    assert all(r.status == 0 for r in out.values())
+    assert sorted(r.slot for r in out.values()) == [0, 1, 2]
+    assert len(s.batches) == 3 and overlap_seconds(s.batches) > 0.0
+    for k, r in out.items():
+        assert np.array_equal(r.u, alone[k].u), k
+        assert r.iterations == alone[k].iterations
+    s.close()
 
 
 def test_budget_rejection_and_admission():
